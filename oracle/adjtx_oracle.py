@@ -1,0 +1,330 @@
+"""Plain FP64 oracle of the adjusted 2-D transforms.
+
+TEST INFRASTRUCTURE.  This module is the reference the CUDA path is checked
+against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs
+of ``bench.py`` may use it; it shares no code with the CUDA library and imports
+nothing from it.
+
+Source: A. Said, H. E. Egilmez, Y.-H. Chao, "Low-complexity transform
+adjustments for video coding".
+
+Conventions (all in float64):
+
+* A transform matrix has the frequency index k along its rows and the sample
+  index n along its columns; the forward 1-D transform of a line x is y = T x
+  and its inverse is x = T^T y (every matrix here is orthogonal).
+* Cores B are the orthonormal DCT-2, DCT-3, DST-2 and DST-3 (Section 2.1),
+  written from their closed forms.  The DST-7 / DCT-8 targets D of Section 2.2
+  (Eq. 3) are written from theirs.
+* The adjusted 1-D transform is H = C B A (Eq. 1).  A is a band matrix made of
+  layers of disjoint adjacent-pair Givens rotations (Section 2, after Eq. 2, and
+  Section 2.2); layer 0 touches the input first, an even layer rotates pairs
+  (0,1),(2,3),..., an odd layer rotates (1,2),(3,4),...,(N-3,N-2), and a
+  rotation by theta maps (x_i, x_{i+1}) to (c x_i - s x_{i+1}, s x_i + c x_{i+1}).
+  C = diag(Q, I_{N-K}) is the top-left K x K post-adjustment (Section 2.2,
+  Section 2.3: only the first K outputs change).
+* A block is stored row-major with h rows and w columns.  The horizontal
+  transform H_h (w x w) acts along each row, the vertical H_v (h x h) along each
+  column: Y = H_v X H_h^T, and the inverse is X = H_v^T Y H_h (Section 2.2: the
+  adjustments act horizontally and vertically on the whole block).
+
+Every function is the definition written out; numpy matmul is the only library
+step.  There is no blocking, fusion or reordering of the arithmetic beyond
+grouping independent blocks that use the same matrices into one batched
+matmul.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "CORE_DCT2", "CORE_DCT3", "CORE_DST2", "CORE_DST3",
+    "KIND_NONE", "KIND_BAND", "KIND_POST",
+    "dct2", "dct3", "dst2", "dst3", "dst7", "dct8", "dct4",
+    "reversal", "alt_sign", "core_matrix",
+    "layer_pairs", "givens_layer", "band_matrix", "post_matrix",
+    "adjusted_matrix", "tf_matrix",
+    "forward_2d", "inverse_2d", "forward_blocks", "inverse_blocks",
+    "dct2_fast", "dct4_fast",
+    "eq2_weighted_error",
+]
+
+CORE_DCT2, CORE_DCT3, CORE_DST2, CORE_DST3 = 0, 1, 2, 3
+KIND_NONE, KIND_BAND, KIND_POST = 0, 1, 2
+
+
+# --------------------------------------------------------------------------
+# Closed-form trigonometric matrices (Section 1, Section 2.1, Section 2.2).
+# Orthonormal scaling throughout: c_0 = 1/sqrt(2) for the cosine families,
+# d_{N-1} = 1/sqrt(2) for the sine families.
+# --------------------------------------------------------------------------
+
+def _kn(N):
+    k = np.arange(N, dtype=np.float64)[:, None]
+    n = np.arange(N, dtype=np.float64)[None, :]
+    return k, n
+
+
+def dct2(N: int) -> np.ndarray:
+    """DCT-2: T[k,n] = c_k sqrt(2/N) cos(pi (2n+1) k / (2N))."""
+    k, n = _kn(N)
+    T = math.sqrt(2.0 / N) * np.cos(np.pi * (2 * n + 1) * k / (2 * N))
+    T[0, :] *= 1.0 / math.sqrt(2.0)
+    return T
+
+
+def dct3(N: int) -> np.ndarray:
+    """DCT-3: T[k,n] = c_n sqrt(2/N) cos(pi (2k+1) n / (2N))."""
+    k, n = _kn(N)
+    T = math.sqrt(2.0 / N) * np.cos(np.pi * (2 * k + 1) * n / (2 * N))
+    T[:, 0] *= 1.0 / math.sqrt(2.0)
+    return T
+
+
+def dst2(N: int) -> np.ndarray:
+    """DST-2: T[k,n] = d_k sqrt(2/N) sin(pi (2n+1) (k+1) / (2N))."""
+    k, n = _kn(N)
+    T = math.sqrt(2.0 / N) * np.sin(np.pi * (2 * n + 1) * (k + 1) / (2 * N))
+    T[N - 1, :] *= 1.0 / math.sqrt(2.0)
+    return T
+
+
+def dst3(N: int) -> np.ndarray:
+    """DST-3: T[k,n] = d_n sqrt(2/N) sin(pi (2k+1) (n+1) / (2N))."""
+    k, n = _kn(N)
+    T = math.sqrt(2.0 / N) * np.sin(np.pi * (2 * k + 1) * (n + 1) / (2 * N))
+    T[:, N - 1] *= 1.0 / math.sqrt(2.0)
+    return T
+
+
+def dst7(N: int) -> np.ndarray:
+    """DST-7 (Section 2.2): T[k,n] = sqrt(4/(2N+1)) sin(pi (2k+1)(n+1) / (2N+1)).
+
+    The basis index k multiplies (2k+1); the transposed reading is the DST-6
+    and fails Eq. 3 against the DCT-8 below.
+    """
+    k, n = _kn(N)
+    return math.sqrt(4.0 / (2 * N + 1)) * np.sin(np.pi * (2 * k + 1) * (n + 1) / (2 * N + 1))
+
+
+def dct8(N: int) -> np.ndarray:
+    """DCT-8 (Section 2.2): T[k,n] = sqrt(4/(2N+1)) cos(pi (2k+1)(2n+1) / (4N+2))."""
+    k, n = _kn(N)
+    return math.sqrt(4.0 / (2 * N + 1)) * np.cos(np.pi * (2 * k + 1) * (2 * n + 1) / (4 * N + 2))
+
+
+def dct4(N: int) -> np.ndarray:
+    """DCT-4: T[k,n] = sqrt(2/N) cos(pi (2n+1)(2k+1) / (4N)) (odd half of the DCT-2)."""
+    k, n = _kn(N)
+    return math.sqrt(2.0 / N) * np.cos(np.pi * (2 * n + 1) * (2 * k + 1) / (4 * N))
+
+
+def reversal(N: int) -> np.ndarray:
+    """R of Section 2.1: R[m,n] = 1 iff m = N-1-n."""
+    R = np.zeros((N, N))
+    R[np.arange(N), N - 1 - np.arange(N)] = 1.0
+    return R
+
+
+def alt_sign(N: int) -> np.ndarray:
+    """S of Section 2.1: diagonal with S[m,m] = (-1)^m."""
+    return np.diag((-1.0) ** np.arange(N))
+
+
+_CORES = {CORE_DCT2: dct2, CORE_DCT3: dct3, CORE_DST2: dst2, CORE_DST3: dst3}
+
+
+def core_matrix(N: int, core: int) -> np.ndarray:
+    """The fast core B (Section 2.1) as its closed-form matrix."""
+    return _CORES[int(core)](N)
+
+
+# --------------------------------------------------------------------------
+# Adjustments (Eq. 1; Givens factorisation after Eq. 2; Section 2.2).
+# --------------------------------------------------------------------------
+
+def layer_pairs(N: int, parity: int):
+    """Index pairs (i, i+1) rotated by one layer: even from 0, odd from 1, no wrap."""
+    return [(i, i + 1) for i in range(int(parity), N - 1, 2)]
+
+
+def givens_layer(N: int, parity: int, angles) -> np.ndarray:
+    """One layer of parallel adjacent-pair Givens rotations as an N x N matrix."""
+    pairs = layer_pairs(N, parity)
+    angles = np.asarray(angles, dtype=np.float64)
+    if angles.shape != (len(pairs),):
+        raise ValueError(f"layer of parity {parity} at N={N} needs {len(pairs)} angles")
+    G = np.eye(N)
+    for (i, j), th in zip(pairs, angles):
+        c, s = math.cos(th), math.sin(th)
+        G[i, i], G[i, j] = c, -s
+        G[j, i], G[j, j] = s, c
+    return G
+
+
+def band_matrix(N: int, parities, angles) -> np.ndarray:
+    """A = G_{L-1} ... G_1 G_0; the angles of layer 0 come first in ``angles``."""
+    angles = np.asarray(angles, dtype=np.float64).ravel()
+    A = np.eye(N)
+    pos = 0
+    for p in parities:
+        cnt = len(layer_pairs(N, int(p)))
+        A = givens_layer(N, int(p), angles[pos:pos + cnt]) @ A
+        pos += cnt
+    if pos != angles.size:
+        raise ValueError(f"{angles.size} angles given, layers need {pos}")
+    return A
+
+
+def post_matrix(N: int, Q) -> np.ndarray:
+    """C = diag(Q, I_{N-K}): Q acts on the K lowest-frequency outputs."""
+    Q = np.asarray(Q, dtype=np.float64)
+    K = Q.shape[0]
+    if Q.shape != (K, K) or K > N:
+        raise ValueError("Q must be K x K with K <= N")
+    C = np.eye(N)
+    C[:K, :K] = Q
+    return C
+
+
+def adjusted_matrix(N, core, kind, parities=(), angles=(), Q=None) -> np.ndarray:
+    """H = C B A of Eq. 1 for one direction."""
+    B = core_matrix(N, core)
+    if kind == KIND_NONE:
+        return B
+    if kind == KIND_BAND:
+        return B @ band_matrix(N, parities, angles)
+    if kind == KIND_POST:
+        return post_matrix(N, Q) @ B
+    raise ValueError(f"unknown adjustment kind {kind}")
+
+
+def tf_matrix(tf) -> np.ndarray:
+    """H for an object (or dict) carrying n, core, kind, parities, angles, q."""
+    get = (lambda k: tf[k]) if isinstance(tf, dict) else (lambda k: getattr(tf, k))
+    kind = int(get("kind"))
+    return adjusted_matrix(
+        int(get("n")), int(get("core")), kind,
+        parities=get("parities") if kind == KIND_BAND else (),
+        angles=get("angles") if kind == KIND_BAND else (),
+        Q=get("q") if kind == KIND_POST else None,
+    )
+
+
+# --------------------------------------------------------------------------
+# Separable 2-D application (Section 2.2).
+# --------------------------------------------------------------------------
+
+def forward_2d(X, Hh, Hv) -> np.ndarray:
+    """Y = H_v X H_h^T for one block or a stack of blocks (..., h, w)."""
+    X = np.asarray(X, dtype=np.float64)
+    return Hv @ X @ Hh.T
+
+
+def inverse_2d(Y, Hh, Hv) -> np.ndarray:
+    """X = H_v^T Y H_h, the inverse of ``forward_2d`` for orthogonal H."""
+    Y = np.asarray(Y, dtype=np.float64)
+    return Hv.T @ Y @ Hh
+
+
+def _apply_blocks(src, blocks, tfs, fn):
+    src = np.asarray(src)
+    out = np.zeros(src.shape[0], dtype=np.float64)
+    mats = {}
+
+    def H(i):
+        if i not in mats:
+            mats[i] = tf_matrix(tfs[i])
+        return mats[i]
+
+    off = np.asarray(blocks["offset"], dtype=np.int64)
+    key = np.stack([np.asarray(blocks[f], dtype=np.int64)
+                    for f in ("w", "h", "tf_h", "tf_v")], axis=1)
+    if key.shape[0] == 0:
+        return out
+    uniq, inv = np.unique(key, axis=0, return_inverse=True)
+    inv = inv.ravel()
+    for g, (w, h, th, tv) in enumerate(uniq):
+        sel = off[inv == g]
+        idx = sel[:, None] + np.arange(w * h)[None, :]
+        X = src[idx].astype(np.float64).reshape(-1, h, w)
+        out[idx] = fn(X, H(int(th)), H(int(tv))).reshape(-1, w * h)
+    return out
+
+
+def forward_blocks(x_flat, blocks, tfs) -> np.ndarray:
+    """FP64 forward transform of every block of a packed block-linear buffer.
+
+    ``blocks`` has fields offset, w, h, tf_h, tf_v; ``tfs[i]`` describes 1-D
+    transform i.  Positions not covered by a block are left at zero.
+    """
+    return _apply_blocks(x_flat, blocks, tfs, forward_2d)
+
+
+def inverse_blocks(y_flat, blocks, tfs) -> np.ndarray:
+    """FP64 inverse transform of every block (see ``forward_blocks``)."""
+    return _apply_blocks(y_flat, blocks, tfs, inverse_2d)
+
+
+# --------------------------------------------------------------------------
+# The oracle's own FP64 fast DCT-2 (Section 1 / 2.1: the even/odd structure that
+# makes the DCT-2 family cheap).  Checked against the closed form in the tests.
+# --------------------------------------------------------------------------
+
+def dct2_fast(x) -> np.ndarray:
+    """Orthonormal DCT-2 of a line by even/odd recursion.
+
+    The even outputs are the half-length DCT-2 of (x_n + x_{N-1-n})/sqrt(2);
+    the odd outputs are the half-length DCT-4 of (x_n - x_{N-1-n})/sqrt(2).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    N = x.shape[-1]
+    if N == 1:
+        return x.copy()
+    h = N // 2
+    head, tail = x[..., :h], x[..., ::-1][..., :h]
+    y = np.empty_like(x)
+    y[..., 0::2] = dct2_fast((head + tail) / math.sqrt(2.0))
+    y[..., 1::2] = dct4_fast((head - tail) / math.sqrt(2.0))
+    return y
+
+
+def dct4_fast(x) -> np.ndarray:
+    """Orthonormal DCT-4 of length M via an M/2-point complex DFT.
+
+    Pair a_m = x_{2m} with b_m = x_{M-1-2m}, form z_m = (a_m - i b_m) e^{i pi m / M},
+    take Z_p = sum_m z_m e^{2 pi i m p / (M/2)} and W_p = sqrt(2/M) Z_p
+    e^{i pi (4p+1) / (4M)}; then X_{2p} = Re W_p and X_{M-1-2p} = Im W_p.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    M = x.shape[-1]
+    if M == 1:
+        return x.copy()
+    P = M // 2
+    m = np.arange(P)
+    a = x[..., 2 * m]
+    b = x[..., M - 1 - 2 * m]
+    z = (a - 1j * b) * np.exp(1j * np.pi * m / M)
+    Z = np.fft.ifft(z, axis=-1) * P
+    W = math.sqrt(2.0 / M) * Z * np.exp(1j * np.pi * (4 * m + 1) / (4 * M))
+    X = np.empty_like(x)
+    X[..., 2 * m] = W.real
+    X[..., M - 1 - 2 * m] = W.imag
+    return X
+
+
+# --------------------------------------------------------------------------
+# Design criterion (Eq. 2).
+# --------------------------------------------------------------------------
+
+def eq2_weighted_error(H, D) -> float:
+    """sum_i sum_j e^{-alpha i} (H_ij - D_ij)^2 with alpha = ln(10^2)/N (Eq. 2)."""
+    H = np.asarray(H, dtype=np.float64)
+    D = np.asarray(D, dtype=np.float64)
+    N = H.shape[0]
+    alpha = math.log(100.0) / N
+    w = np.exp(-alpha * np.arange(N))[:, None]
+    return float(np.sum(w * (H - D) ** 2))
