@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput of the fused adjusted 2-D transforms (forward + inverse) on one GB300.
+
+A step is one forward and one inverse transform of the whole batch: the mixed-size
+workload of 8 synthetic 3840x2160 frames (66.4 M coefficients, ~0.5 M blocks of
+4..64 x 4..64, every block with its own core x adjustment per direction).  The
+metric is coefficients / (t_forward + t_inverse) in Gcoef/s, with the inputs
+resident in HBM; L2 is flushed (256 MiB write) before every timed kernel and the
+kernels are timed with CUDA events on their stream.
+
+Extra fields: `e2e` (the same metric through the host-buffer C-ABI entry points,
+copies included), `roofline` (HBM roofline of the dominant kernel from
+algorithmic bytes), `cpu_baseline` (the FP64 oracle on the host cores) and the
+SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcoef/s fwd+inv adjusted 2-D transforms (mixed 4-64)"
+UNIT = "Gcoef/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="fused", choices=["fused", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--frames", type=int, default=8, help="frames of the workload (profiling uses fewer)")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(rank=0, frames=8):
+    import synth
+    # every rank transforms its own seeded batch of the same shape (weak scaling)
+    return synth.config3(seed=3 + 1000 * rank, frames=frames)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2505_23618_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    src = None
+    for ln in lines:
+        if ln.startswith("source_hash"):
+            src = ln.split()[-1]
+    if src != kernel_source_hash():
+        return None
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) >= 2 and parts[0] == kernel:
+            return float(parts[1])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for ln in (self.out or "").splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(sample_desc="full workload (66.4 M coefficients), one forward + one inverse"):
+    """Time the FP64 oracle on the host (single process, BLAS pinned to 1 thread)."""
+    code = (
+        "import time, json, sys; sys.path.insert(0, %r)\n"
+        "import numpy as np, synth, oracle\n"
+        "wl = synth.config3()\n"
+        "t = time.perf_counter(); y = oracle.forward_blocks(wl.data, wl.blocks, wl.tfs)\n"
+        "x = oracle.inverse_blocks(y, wl.blocks, wl.tfs); dt = time.perf_counter() - t\n"
+        "print(json.dumps({'coefs': int(wl.total), 'seconds': dt}))\n" % ROOT)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc,
+                "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["coefs"] / d["seconds"] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": sample_desc, "seconds": round(d["seconds"], 3)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import synth
+    wl = workload(0)
+    # each step transforms a bounded sample of the workload: the first ~1 M coefficients
+    cs = np.cumsum(wl.blocks["w"].astype(np.int64) * wl.blocks["h"])
+    nb = int(np.searchsorted(cs, 1_000_000)) + 1
+    blocks, tot = wl.blocks[:nb], int(cs[nb - 1])
+    data = wl.data[:tot]
+    for _ in range(args.warmup):
+        oracle.inverse_blocks(oracle.forward_blocks(data, blocks, wl.tfs), blocks, wl.tfs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.inverse_blocks(oracle.forward_blocks(data, blocks, wl.tfs), blocks, wl.tfs)
+    dt = time.perf_counter() - t0
+    value = tot * args.steps / dt / 1e9
+    sample = f"first {nb} blocks ({tot} coefficients) of the workload per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "coefs": tot, "blocks": nb, "what": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fused(args):
+    import numpy as np
+    import torch
+
+    import paper_2505_23618_gb300 as adj
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = workload(rank, args.frames)
+    coefs = wl.total
+    plan = adj.Plan(wl.tfs)
+    plan.set_blocks(wl.blocks, coefs)
+    info = plan.info()
+    stream = torch.cuda.current_stream(dev)
+
+    x = torch.from_numpy(wl.data).to(dev)
+    y = torch.empty(coefs, dtype=torch.float32, device=dev)
+    xr = torch.empty(coefs, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        flush.fill_(1.0)
+        if ev:
+            ev[0].record(stream)
+        plan.fwd(x, y, stream)
+        if ev:
+            ev[1].record(stream)
+        flush.fill_(2.0)
+        if ev:
+            ev[2].record(stream)
+        plan.inv(y, xr, stream)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    # correctness guard on the timed buffers (round trip), outside the timed region
+    rt = float((xr - x.float()).abs().max())
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            step(events[k])
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t_fwd = np.array([e[0].elapsed_time(e[1]) for e in events]) * 1e-3
+    t_inv = np.array([e[2].elapsed_time(e[3]) for e in events]) * 1e-3
+    t_total = float(t_fwd.sum() + t_inv.sum())
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = coefs * world * args.steps / t_total / 1e9
+
+    # end to end through the host-buffer C-ABI calls (pinned memory), copies included
+    h_x = torch.from_numpy(wl.data).pin_memory()
+    h_y = torch.empty(coefs, dtype=torch.float32).pin_memory()
+    h_xr = torch.empty(coefs, dtype=torch.float32).pin_memory()
+    plan.fwd_host(h_x, h_y, stream)
+    plan.inv_host(h_y, h_xr, stream)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.fwd_host(h_x, h_y, stream)
+        plan.inv_host(h_y, h_xr, stream)
+    e2e_t = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    e2e_value = coefs * world / e2e_t / 1e9
+
+    # roofline of the dominant kernel (algorithmic bytes per launch / mean duration)
+    nb = int(wl.blocks.size)
+    meta = info["n_tiles"] * 16 + nb * 4
+    kern = {
+        "fwd": {"bytes": coefs * 6 + meta, "ms": float(t_fwd.mean() * 1e3)},
+        "inv": {"bytes": coefs * 8 + meta, "ms": float(t_inv.mean() * 1e3)},
+    }
+    peak, peak_src = measured_peak()
+    for k in kern.values():
+        k["gbs"] = k["bytes"] / (k["ms"] * 1e-3) / 1e9
+        k["frac"] = k["gbs"] / peak
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    traffic = profiled_traffic(dom)
+    roof = {"bound": "hbm", "achieved": round(kern[dom]["gbs"], 1), "peak": peak, "unit": "GB/s",
+            "frac": round(kern[dom]["frac"], 4), "traffic": traffic, "kernel": f"fused_kernel<{dom}>",
+            "algorithmic_bytes_per_launch": kern[dom]["bytes"], "peak_source": peak_src + " hbm_gbs"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_total / args.steps * 1e3, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "coefs_per_gpu": coefs, "blocks_per_gpu": nb,
+                       "tiles": info["n_tiles"], "grid": info["grid_fwd"], "threads": info["threads"],
+                       "l2": "flushed by a 256 MiB write before every timed kernel",
+                       "layout": "packed block-linear int16 in, FP32 coefficients / reconstruction out"},
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": coefs * (2 + 4),
+                    "d2h_bytes_per_step": coefs * (4 + 4)},
+            "gpu_launches": 2 * args.steps,
+            "roofline": roof,
+            "kernels": {k: {"ms": round(v["ms"], 4), "GB/s": round(v["gbs"], 1), "frac": round(v["frac"], 4)}
+                        for k, v in kern.items()},
+            "clocks": clk.summary(),
+            "roundtrip_max_abs_err": rt,
+        }
+        if not args.no_cpu_baseline and world == 1 and args.frames == 8:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_fused(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * adjtx.h — C ABI of the GB300 (sm_103a) adjusted-transform library.
+ *
+ * The library computes batched, separable 2-D "adjusted" trigonometric
+ * transforms of residual blocks, after A. Said, H. E. Egilmez, Y.-H. Chao,
+ * "Low-complexity transform adjustments for video coding":
+ *
+ *   1-D transform of length N (Eq. 1):  H = C B A
+ *     B  fast core, one of DCT-2, DCT-3, DST-2, DST-3 (Section 2.1: DCT-3 = DCT-2^T,
+ *        DST-2 = R DCT-2 S, DST-3 = S DCT-2^T R), orthonormal;
+ *     A  band pre-adjustment (Section 2, after Eq. 2; Section 2.2, item 1): layers of
+ *        disjoint adjacent-pair Givens rotations, layer 0 applied first; an even layer
+ *        rotates pairs (0,1),(2,3),..., an odd layer (1,2),(3,4),...,(N-3,N-2); the
+ *        rotation by theta maps (x_i, x_{i+1}) to (c x_i - s x_{i+1}, s x_i + c x_{i+1});
+ *     C  post-adjustment diag(Q, I_{N-K}) with Q a K x K orthogonal matrix acting on the K
+ *        lowest-frequency outputs (Section 2.2, item 2; Section 2.3).
+ *   2-D forward of an h x w row-major block X (Section 2.2: the adjustments act
+ *   horizontally and vertically on the whole block):  Y = H_v X H_h^T  (row pass with
+ *   the horizontal transform H_h of length w, column pass with the vertical H_v of length h);
+ *   2-D inverse:  X = H_v^T Y H_h.
+ *
+ * Everything runs on one GPU in hand-written CUDA.  There is no CPU fallback: every
+ * call that computes launches kernels, and fails with ADJ_ERR_CUDA when no usable
+ * device is present.
+ *
+ * Conventions
+ *   - All calls return ADJ_OK (0) or a negative ADJ_ERR_* code; nothing aborts or
+ *     throws across this boundary.  adj_last_error() returns a message for the last
+ *     failing call of the calling thread.
+ *   - "stream" arguments are cudaStream_t values passed as void* (NULL = legacy
+ *     default stream).  Device entry points are asynchronous with respect to the host:
+ *     a kernel fault surfaces at the caller's next synchronisation.
+ *   - Device buffers are owned by the caller; the library never allocates or frees
+ *     them.  A plan owns its parameter tables, tile lists and work counters, all
+ *     allocated by adj_plan_create / adj_plan_set_blocks, and the staging buffers of
+ *     the *_host entry points (allocated on their first call).
+ *   - Calls that use one plan must not run concurrently on the GPU (one stream, or
+ *     serialised by the caller): the plan's work counters are shared by its launches.
+ */
+#ifndef ADJTX_H
+#define ADJTX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ADJ_OK = 0,
+  ADJ_ERR_INVALID_ARG = -1,      /* null pointer, bad enum, bad count, overlapping blocks */
+  ADJ_ERR_UNSUPPORTED_SIZE = -2, /* N or block side not in {4, 8, 16, 32, 64}, K > N, too many layers */
+  ADJ_ERR_PARAM_MISMATCH = -3,   /* block side != its transform's N; angle count; non-orthogonal Q;
+                                    update_params that changes structure */
+  ADJ_ERR_MISALIGNED = -4,       /* block offset not a multiple of 16 samples; buffer not 16-B aligned */
+  ADJ_ERR_CUDA = -5,             /* a CUDA runtime call failed (message in adj_last_error) */
+  ADJ_ERR_NO_BLOCKS = -6         /* transform called before adj_plan_set_blocks */
+};
+
+/* Core B (Section 2.1). */
+typedef enum { ADJ_CORE_DCT2 = 0, ADJ_CORE_DCT3 = 1, ADJ_CORE_DST2 = 2, ADJ_CORE_DST3 = 3 } adj_core_t;
+/* Adjustment (Section 2.2): none, band pre-adjustment A, or top-left post-adjustment C. */
+typedef enum { ADJ_ADJ_NONE = 0, ADJ_ADJ_PRE_BAND = 1, ADJ_ADJ_POST_BLOCK = 2 } adj_kind_t;
+
+#define ADJ_MAX_LAYERS 64
+
+/* One 1-D adjusted transform H = C B A of length n.  Host memory, read during the call
+ * that receives it (copied; the caller may free it afterwards). */
+typedef struct {
+  int32_t n;                    /* 4, 8, 16, 32 or 64 */
+  int32_t core;                 /* adj_core_t */
+  int32_t kind;                 /* adj_kind_t */
+  int32_t n_layers;             /* band: number of rotation layers, 0..ADJ_MAX_LAYERS */
+  const uint8_t* layer_parity;  /* band: n_layers entries, 0 = even pairs, 1 = odd pairs */
+  const double* angles;         /* band: angles of layer 0 first; n/2 per even layer,
+                                   n/2 - 1 per odd layer */
+  int32_t k;                    /* post: size K of Q, 1 <= K <= n */
+  const double* q;              /* post: K x K row-major, orthogonal to 1e-6 */
+} adj_1d_desc_t;
+
+/* One residual block: h rows x w columns, row-major, starting at element `offset` of
+ * the packed buffers.  tf_h / tf_v index the plan's 1-D transforms (tfs[tf_h].n == w,
+ * tfs[tf_v].n == h).  16 bytes. */
+typedef struct {
+  int64_t offset;  /* in samples; multiple of 16 */
+  uint16_t w, h;
+  uint16_t tf_h, tf_v;
+} adj_block_t;
+
+typedef struct adj_plan adj_plan_t;
+
+/* Plan flags. */
+#define ADJ_PLAN_DEFAULT 0
+
+/*
+ * Create a plan for a table of 1-D transforms (Eq. 1 per entry).
+ * Validates every entry, materialises the parameters on the host in FP64 (cos/sin of
+ * each angle; Q padded to a power of two with the identity, i.e. the top-left block of
+ * C = diag(Q, I)) and uploads them as FP32 to the current device.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, PARAM_MISMATCH, CUDA.  On error *plan is NULL.
+ */
+int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, int32_t flags);
+
+/*
+ * Give the plan its block list (host memory, n_blocks records) for buffers of
+ * total_coefs samples.  Validates sizes, transform indices, alignment, bounds and
+ * non-overlap; groups blocks of equal (w, h, tf_h, tf_v) into shared-memory tiles in
+ * storage order and uploads the tile list.  May be called again to replace the list.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, PARAM_MISMATCH, MISALIGNED, CUDA.
+ */
+int adj_plan_set_blocks(adj_plan_t* plan, const adj_block_t* blocks, int64_t n_blocks,
+                        int64_t total_coefs);
+
+/*
+ * Replace the parameter values (angles, Q) of all transforms without changing their
+ * structure (n, core, kind, layer parities, K).  Asynchronous on the legacy stream
+ * ordering of cudaMemcpy: completes before it returns.
+ * Errors: INVALID_ARG, PARAM_MISMATCH, CUDA.
+ */
+int adj_plan_update_params(adj_plan_t* plan, const adj_1d_desc_t* tfs, int32_t n_tfs);
+
+/*
+ * Forward 2-D transform of every block: d_resid (int16, device, total_coefs samples,
+ * 16-B aligned) -> d_coef (FP32, device, total_coefs, 16-B aligned), Y = H_v X H_h^T.
+ * Samples outside every block are not written.  One persistent kernel launch.
+ */
+int adj_transform_fwd(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, void* stream);
+
+/*
+ * Inverse 2-D transform: d_coef (FP32, device) -> d_resid_out (FP32, device, not
+ * rounded), X = H_v^T Y H_h.  Same layout and alignment rules as adj_transform_fwd.
+ */
+int adj_transform_inv(adj_plan_t* plan, const float* d_coef, float* d_resid_out, void* stream);
+
+/*
+ * Host-buffer variants: copy the input from host memory to plan-owned device staging
+ * buffers, transform, copy the result back and wait for it.  Page-locked host memory
+ * gives full copy bandwidth.  The staging buffers are allocated on the first call.
+ */
+int adj_transform_fwd_host(adj_plan_t* plan, const int16_t* h_resid, float* h_coef, void* stream);
+int adj_transform_inv_host(adj_plan_t* plan, const float* h_coef, float* h_resid_out, void* stream);
+
+/* Launch geometry and tile statistics of a plan (for benchmarks and tests). */
+typedef struct {
+  int64_t n_blocks;
+  int64_t total_coefs;
+  int32_t n_tiles;
+  int32_t grid_fwd, grid_inv;   /* persistent CTAs per launch */
+  int32_t threads;              /* threads per CTA */
+  int32_t smem_bytes;           /* dynamic shared memory per CTA */
+  int32_t n_sm;
+} adj_plan_info_t;
+int adj_plan_info(const adj_plan_t* plan, adj_plan_info_t* info);
+
+/* Release everything the plan owns.  Safe on NULL. */
+void adj_plan_destroy(adj_plan_t* plan);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* adj_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADJTX_H */

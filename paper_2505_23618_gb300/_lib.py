@@ -1,0 +1,201 @@
+"""ctypes binding of the C ABI in include/adjtx.h (argument marshalling only).
+
+Every transform runs in the CUDA library; if ``_build/libadjtx.so`` is missing the
+import fails loudly (build it with ``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libadjtx.so")
+
+ADJ_OK = 0
+ERRORS = {
+    -1: "ADJ_ERR_INVALID_ARG",
+    -2: "ADJ_ERR_UNSUPPORTED_SIZE",
+    -3: "ADJ_ERR_PARAM_MISMATCH",
+    -4: "ADJ_ERR_MISALIGNED",
+    -5: "ADJ_ERR_CUDA",
+    -6: "ADJ_ERR_NO_BLOCKS",
+}
+ERR_CODE = {v: k for k, v in ERRORS.items()}
+
+EXPORTED = (
+    "adj_plan_create", "adj_plan_set_blocks", "adj_plan_update_params",
+    "adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host",
+    "adj_transform_inv_host", "adj_plan_info", "adj_plan_destroy", "adj_last_error",
+)
+
+
+class Adj1dDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("core", C.c_int32), ("kind", C.c_int32),
+                ("n_layers", C.c_int32), ("layer_parity", C.POINTER(C.c_uint8)),
+                ("angles", C.POINTER(C.c_double)), ("k", C.c_int32),
+                ("q", C.POINTER(C.c_double))]
+
+
+class AdjPlanInfo(C.Structure):
+    _fields_ = [("n_blocks", C.c_int64), ("total_coefs", C.c_int64), ("n_tiles", C.c_int32),
+                ("grid_fwd", C.c_int32), ("grid_inv", C.c_int32), ("threads", C.c_int32),
+                ("smem_bytes", C.c_int32), ("n_sm", C.c_int32)]
+
+
+BLOCK_DTYPE = np.dtype([("offset", "<i8"), ("w", "<u2"), ("h", "<u2"),
+                        ("tf_h", "<u2"), ("tf_v", "<u2")])
+
+
+class AdjError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"adjtx CUDA library not built ({path} missing); run the build first")
+    lib = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    lib.adj_plan_create.argtypes = [C.POINTER(vp), C.POINTER(Adj1dDesc), i32, i32]
+    lib.adj_plan_set_blocks.argtypes = [vp, vp, i64, i64]
+    lib.adj_plan_update_params.argtypes = [vp, C.POINTER(Adj1dDesc), i32]
+    for f in ("adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host", "adj_transform_inv_host"):
+        getattr(lib, f).argtypes = [vp, vp, vp, vp]
+    lib.adj_plan_info.argtypes = [vp, C.POINTER(AdjPlanInfo)]
+    lib.adj_plan_destroy.argtypes = [vp]
+    lib.adj_plan_destroy.restype = None
+    lib.adj_last_error.restype = C.c_char_p
+    for f in EXPORTED:
+        if f not in ("adj_plan_destroy", "adj_last_error"):
+            getattr(lib, f).restype = C.c_int
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def check(rc: int):
+    if rc != ADJ_OK:
+        raise AdjError(rc, lib().adj_last_error().decode())
+
+
+def _get(tf, name, default=None):
+    if isinstance(tf, dict):
+        return tf.get(name, default)
+    return getattr(tf, name, default)
+
+
+class _DescArray:
+    """Keeps the numpy buffers referenced by an array of Adj1dDesc alive."""
+
+    def __init__(self, tfs):
+        self.keep = []
+        self.arr = (Adj1dDesc * max(1, len(tfs)))()
+        for i, tf in enumerate(tfs):
+            d = self.arr[i]
+            d.n, d.core, d.kind = int(_get(tf, "n")), int(_get(tf, "core")), int(_get(tf, "kind", 0))
+            par = np.ascontiguousarray(_get(tf, "parities", np.zeros(0)), dtype=np.uint8)
+            ang = np.ascontiguousarray(_get(tf, "angles", np.zeros(0)), dtype=np.float64)
+            q = _get(tf, "q", None)
+            if d.kind == 1:
+                d.n_layers = par.size
+                d.layer_parity = par.ctypes.data_as(C.POINTER(C.c_uint8))
+                d.angles = ang.ctypes.data_as(C.POINTER(C.c_double))
+                self.keep += [par, ang]
+            if d.kind == 2 and q is not None:
+                qa = np.ascontiguousarray(q, dtype=np.float64)
+                d.k = qa.shape[0]
+                d.q = qa.ctypes.data_as(C.POINTER(C.c_double))
+                self.keep.append(qa)
+        self.n = len(tfs)
+
+
+def _ptr(x) -> int:
+    """Address of a torch tensor / numpy array / int."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(getattr(s, "cuda_stream", s))
+
+
+class Plan:
+    """An adj_plan_t: 1-D transform table + block list, with fwd/inv entry points."""
+
+    def __init__(self, tfs, flags: int = 0):
+        self._lib = lib()
+        self.tfs = list(tfs)
+        self._h = C.c_void_p()
+        d = _DescArray(self.tfs)
+        check(self._lib.adj_plan_create(C.byref(self._h), d.arr, d.n, flags))
+        self.total = 0
+
+    def set_blocks(self, blocks: np.ndarray, total: int):
+        b = np.ascontiguousarray(blocks).view(BLOCK_DTYPE)
+        check(self._lib.adj_plan_set_blocks(self._h, b.ctypes.data if b.size else None,
+                                            b.size, int(total)))
+        self.total = int(total)
+        return self
+
+    def update_params(self, tfs):
+        d = _DescArray(list(tfs))
+        check(self._lib.adj_plan_update_params(self._h, d.arr, d.n))
+        self.tfs = list(tfs)
+
+    def fwd(self, d_in, d_out, stream=None):
+        check(self._lib.adj_transform_fwd(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+    def inv(self, d_in, d_out, stream=None):
+        check(self._lib.adj_transform_inv(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+    def fwd_host(self, h_in, h_out, stream=None):
+        check(self._lib.adj_transform_fwd_host(self._h, _ptr(h_in), _ptr(h_out), _stream(stream)))
+
+    def inv_host(self, h_in, h_out, stream=None):
+        check(self._lib.adj_transform_inv_host(self._h, _ptr(h_in), _ptr(h_out), _stream(stream)))
+
+    def info(self) -> dict:
+        i = AdjPlanInfo()
+        check(self._lib.adj_plan_info(self._h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in AdjPlanInfo._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.adj_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,443 @@
+// C ABI of the adjusted-transform library: plan creation, validation, parameter
+// materialisation, tiling and the transform entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "adjtx.h"
+#include "adjtx_kernels.h"
+
+using namespace adjtx;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(ADJ_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call)                                 \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+bool is_size(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; }
+
+int pairs_in_layer(int n, int parity) { return parity ? n / 2 - 1 : n / 2; }
+
+struct TfHost {
+  int n, core, kind, n_layers, k, kt, n_pairs;
+  std::vector<uint8_t> parity;
+  std::vector<double> angles;
+  std::vector<double> q;  // k x k
+};
+
+}  // namespace
+
+struct adj_plan {
+  int device = 0;
+  int n_sm = 0;
+  int threads = 64;
+  std::vector<TfHost> tfs;
+  TfDev* d_tfs = nullptr;
+  float* d_params = nullptr;
+  size_t n_params = 0;
+  bool has_blocks = false;
+  int64_t n_blocks = 0;
+  int64_t total = 0;
+  TileDev* d_tiles = nullptr;
+  uint32_t* d_tile_blk = nullptr;
+  int n_tiles = 0;
+  unsigned* d_counter = nullptr;  // [0..1] forward, [2..3] inverse
+  int grid_fwd = 0, grid_inv = 0;
+  void* d_host_in = nullptr;
+  float* d_host_out = nullptr;
+  size_t host_cap = 0;
+};
+
+namespace {
+
+int validate_tf(const adj_1d_desc_t& d, int idx, TfHost* out) {
+  if (!is_size(d.n)) return fail(ADJ_ERR_UNSUPPORTED_SIZE, "tf %d: n=%d not in {4,8,16,32,64}", idx, d.n);
+  if (d.core < 0 || d.core > 3) return fail(ADJ_ERR_INVALID_ARG, "tf %d: core %d", idx, d.core);
+  if (d.kind < 0 || d.kind > 2) return fail(ADJ_ERR_INVALID_ARG, "tf %d: kind %d", idx, d.kind);
+  TfHost t{};
+  t.n = d.n;
+  t.core = d.core;
+  t.kind = d.kind;
+  if (d.kind == ADJ_ADJ_PRE_BAND) {
+    if (d.n_layers < 0 || d.n_layers > ADJ_MAX_LAYERS)
+      return fail(ADJ_ERR_UNSUPPORTED_SIZE, "tf %d: %d layers (max %d)", idx, d.n_layers, ADJ_MAX_LAYERS);
+    if (d.n_layers > 0 && !d.layer_parity) return fail(ADJ_ERR_INVALID_ARG, "tf %d: null layer_parity", idx);
+    t.n_layers = d.n_layers;
+    int np = 0;
+    for (int l = 0; l < d.n_layers; ++l) {
+      if (d.layer_parity[l] > 1) return fail(ADJ_ERR_INVALID_ARG, "tf %d: parity of layer %d is %d", idx, l, d.layer_parity[l]);
+      t.parity.push_back(d.layer_parity[l]);
+      np += pairs_in_layer(d.n, d.layer_parity[l]);
+    }
+    if (np > 0 && !d.angles) return fail(ADJ_ERR_INVALID_ARG, "tf %d: null angles", idx);
+    t.n_pairs = np;
+    t.angles.assign(d.angles, d.angles + np);
+    for (double a : t.angles)
+      if (!std::isfinite(a)) return fail(ADJ_ERR_PARAM_MISMATCH, "tf %d: non-finite angle", idx);
+  } else if (d.kind == ADJ_ADJ_POST_BLOCK) {
+    if (d.k < 1 || d.k > d.n) return fail(ADJ_ERR_UNSUPPORTED_SIZE, "tf %d: K=%d with n=%d", idx, d.k, d.n);
+    if (!d.q) return fail(ADJ_ERR_INVALID_ARG, "tf %d: null q", idx);
+    t.k = d.k;
+    int kt = 4;
+    while (kt < d.k) kt *= 2;
+    t.kt = kt;
+    t.q.assign(d.q, d.q + (size_t)d.k * d.k);
+    double worst = 0.0;
+    for (int i = 0; i < d.k; ++i)
+      for (int j = 0; j < d.k; ++j) {
+        double s = 0.0;
+        for (int r = 0; r < d.k; ++r) s += t.q[r * d.k + i] * t.q[r * d.k + j];
+        if (!std::isfinite(s)) return fail(ADJ_ERR_PARAM_MISMATCH, "tf %d: non-finite Q", idx);
+        worst = std::max(worst, std::fabs(s - (i == j ? 1.0 : 0.0)));
+      }
+    if (worst > 1e-6) return fail(ADJ_ERR_PARAM_MISMATCH, "tf %d: Q not orthogonal (|Q^T Q - I| = %g)", idx, worst);
+  }
+  *out = std::move(t);
+  return ADJ_OK;
+}
+
+// FP64 -> FP32 parameter materialisation (cos/sin of every angle; padded Q).
+void materialise(const std::vector<TfHost>& tfs, std::vector<float>* params, std::vector<TfDev>* devs) {
+  params->clear();
+  devs->clear();
+  for (const TfHost& t : tfs) {
+    TfDev d{};
+    d.n = t.n;
+    d.core = t.core;
+    d.kind = t.kind;
+    if (t.kind == ADJ_ADJ_PRE_BAND) {
+      d.n_layers = t.n_layers;
+      d.n_pairs = t.n_pairs;
+      for (int l = 0; l < t.n_layers; ++l) {
+        if (t.parity[l]) {
+          if (l < 32) d.par_lo |= 1u << l;
+          else d.par_hi |= 1u << (l - 32);
+        }
+      }
+      if (params->size() % 2) params->push_back(0.f);
+      d.cs_off = (uint32_t)(params->size() / 2);
+      for (double a : t.angles) {
+        params->push_back((float)std::cos(a));
+        params->push_back((float)std::sin(a));
+      }
+    } else if (t.kind == ADJ_ADJ_POST_BLOCK) {
+      d.kt = t.kt;
+      while (params->size() % 4) params->push_back(0.f);
+      d.q_off = (uint32_t)params->size();
+      for (int i = 0; i < t.kt; ++i)
+        for (int j = 0; j < t.kt; ++j) {
+          double v = (i < t.k && j < t.k) ? t.q[i * t.k + j] : (i == j ? 1.0 : 0.0);
+          params->push_back((float)v);
+        }
+    }
+    devs->push_back(d);
+  }
+  while (params->size() % 4) params->push_back(0.f);
+  if (params->empty()) params->resize(4, 0.f);
+}
+
+int upload_params(adj_plan* p) {
+  std::vector<float> params;
+  std::vector<TfDev> devs;
+  materialise(p->tfs, &params, &devs);
+  if (!p->d_params) {
+    CUDA_TRY(cudaMalloc(&p->d_params, params.size() * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&p->d_tfs, std::max<size_t>(1, devs.size()) * sizeof(TfDev)));
+    p->n_params = params.size();
+  } else if (params.size() != p->n_params) {
+    return fail(ADJ_ERR_PARAM_MISMATCH, "parameter size changed");
+  }
+  CUDA_TRY(cudaMemcpy(p->d_params, params.data(), params.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (!devs.empty())
+    CUDA_TRY(cudaMemcpy(p->d_tfs, devs.data(), devs.size() * sizeof(TfDev), cudaMemcpyHostToDevice));
+  return ADJ_OK;
+}
+
+void free_blocks(adj_plan* p) {
+  cudaFree(p->d_tiles);
+  cudaFree(p->d_tile_blk);
+  p->d_tiles = nullptr;
+  p->d_tile_blk = nullptr;
+  p->n_tiles = 0;
+  p->has_blocks = false;
+}
+
+int check_ptr(const void* ptr, const char* name) {
+  if (!ptr) return fail(ADJ_ERR_INVALID_ARG, "%s is null", name);
+  if (reinterpret_cast<uintptr_t>(ptr) % 16) return fail(ADJ_ERR_MISALIGNED, "%s is not 16-byte aligned", name);
+  return ADJ_OK;
+}
+
+int run(adj_plan* p, bool inverse, const void* in, float* out, cudaStream_t stream) {
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  int rc;
+  if ((rc = check_ptr(in, "input")) || (rc = check_ptr(out, "output"))) return rc;
+  if (p->n_tiles == 0) return ADJ_OK;
+  FusedArgs a{};
+  a.tiles = p->d_tiles;
+  a.tile_blk = p->d_tile_blk;
+  a.tfs = p->d_tfs;
+  a.params = p->d_params;
+  a.in = in;
+  a.out = out;
+  a.counter = p->d_counter + (inverse ? 2 : 0);
+  a.n_tiles = p->n_tiles;
+  cudaError_t e = launch_fused(inverse, p->threads, inverse ? p->grid_inv : p->grid_fwd, a, stream);
+  if (e != cudaSuccess) return cuda_fail(e, inverse ? "inverse launch" : "forward launch");
+  return ADJ_OK;
+}
+
+int ensure_host_staging(adj_plan* p) {
+  const size_t need = (size_t)std::max<int64_t>(p->total, 4) * sizeof(float);
+  if (p->host_cap >= need) return ADJ_OK;
+  cudaFree(p->d_host_in);
+  cudaFree(p->d_host_out);
+  p->d_host_in = nullptr;
+  p->d_host_out = nullptr;
+  p->host_cap = 0;
+  CUDA_TRY(cudaMalloc(&p->d_host_in, need));
+  CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->d_host_out), need));
+  CUDA_TRY(cudaMemset(p->d_host_out, 0, need));
+  p->host_cap = need;
+  return ADJ_OK;
+}
+
+int run_host(adj_plan* p, bool inverse, const void* h_in, float* h_out, cudaStream_t stream) {
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  if (!h_in || !h_out) return fail(ADJ_ERR_INVALID_ARG, "null host buffer");
+  int rc = ensure_host_staging(p);
+  if (rc) return rc;
+  const size_t in_bytes = (size_t)p->total * (inverse ? 4 : 2);
+  const size_t out_bytes = (size_t)p->total * 4;
+  CUDA_TRY(cudaMemcpyAsync(p->d_host_in, h_in, in_bytes, cudaMemcpyHostToDevice, stream));
+  rc = run(p, inverse, p->d_host_in, p->d_host_out, stream);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(h_out, p->d_host_out, out_bytes, cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  return ADJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* adj_last_error(void) { return g_err.c_str(); }
+
+int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, int32_t flags) {
+  g_err.clear();
+  if (!plan) return fail(ADJ_ERR_INVALID_ARG, "null plan pointer");
+  *plan = nullptr;
+  if (n_tfs < 0 || n_tfs > 65535 || (n_tfs > 0 && !tfs)) return fail(ADJ_ERR_INVALID_ARG, "bad transform table (n_tfs=%d)", n_tfs);
+  if (flags != ADJ_PLAN_DEFAULT) return fail(ADJ_ERR_INVALID_ARG, "unknown flags %d", flags);
+  std::vector<TfHost> hs(n_tfs);
+  for (int i = 0; i < n_tfs; ++i) {
+    int rc = validate_tf(tfs[i], i, &hs[i]);
+    if (rc) return rc;
+  }
+  adj_plan* p = new adj_plan();
+  p->tfs = std::move(hs);
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "device query");
+  }
+  int rc = upload_params(p);
+  if (!rc) {
+    e = cudaMalloc(&p->d_counter, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(p->d_counter, 0, 4 * sizeof(unsigned));
+    if (e != cudaSuccess) rc = cuda_fail(e, "counter allocation");
+  }
+  for (int inv = 0; inv < 2 && !rc; ++inv) {
+    const void* fn = fused_kernel_ptr(inv, p->threads);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
+    if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
+    else (inv ? p->grid_inv : p->grid_fwd) = std::max(1, occ) * p->n_sm;
+  }
+  if (rc) {
+    adj_plan_destroy(p);
+    return rc;
+  }
+  *plan = p;
+  return ADJ_OK;
+}
+
+int adj_plan_update_params(adj_plan_t* p, const adj_1d_desc_t* tfs, int32_t n_tfs) {
+  g_err.clear();
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (n_tfs != (int)p->tfs.size() || (n_tfs > 0 && !tfs))
+    return fail(ADJ_ERR_PARAM_MISMATCH, "update with %d transforms, plan has %zu", n_tfs, p->tfs.size());
+  std::vector<TfHost> hs(n_tfs);
+  for (int i = 0; i < n_tfs; ++i) {
+    int rc = validate_tf(tfs[i], i, &hs[i]);
+    if (rc) return rc;
+    const TfHost &a = hs[i], &b = p->tfs[i];
+    if (a.n != b.n || a.core != b.core || a.kind != b.kind || a.n_layers != b.n_layers || a.parity != b.parity || a.k != b.k)
+      return fail(ADJ_ERR_PARAM_MISMATCH, "tf %d: structure changed", i);
+  }
+  std::vector<TfHost> old = std::move(p->tfs);
+  p->tfs = std::move(hs);
+  int rc = upload_params(p);
+  if (rc) p->tfs = std::move(old);
+  return rc;
+}
+
+int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_blocks, int64_t total_coefs) {
+  g_err.clear();
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (n_blocks < 0 || (n_blocks > 0 && !blocks)) return fail(ADJ_ERR_INVALID_ARG, "bad block list");
+  if (total_coefs < 0 || total_coefs > (int64_t(1) << 36)) return fail(ADJ_ERR_INVALID_ARG, "total_coefs %lld out of range", (long long)total_coefs);
+  const int n_tfs = (int)p->tfs.size();
+  for (int64_t i = 0; i < n_blocks; ++i) {
+    const adj_block_t& b = blocks[i];
+    if (!is_size(b.w) || !is_size(b.h)) return fail(ADJ_ERR_UNSUPPORTED_SIZE, "block %lld: %dx%d", (long long)i, b.w, b.h);
+    if (b.tf_h >= n_tfs || b.tf_v >= n_tfs) return fail(ADJ_ERR_INVALID_ARG, "block %lld: transform index out of range", (long long)i);
+    if (p->tfs[b.tf_h].n != b.w || p->tfs[b.tf_v].n != b.h)
+      return fail(ADJ_ERR_PARAM_MISMATCH, "block %lld: %dx%d with transforms of length %d (h) and %d (v)",
+                  (long long)i, b.w, b.h, p->tfs[b.tf_h].n, p->tfs[b.tf_v].n);
+    if (b.offset < 0 || b.offset % 16) return fail(ADJ_ERR_MISALIGNED, "block %lld: offset %lld", (long long)i, (long long)b.offset);
+    if (b.offset + (int64_t)b.w * b.h > total_coefs) return fail(ADJ_ERR_INVALID_ARG, "block %lld extends past total_coefs", (long long)i);
+  }
+  std::vector<int64_t> order(n_blocks);
+  for (int64_t i = 0; i < n_blocks; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return blocks[a].offset < blocks[b].offset; });
+  for (int64_t i = 1; i < n_blocks; ++i) {
+    const adj_block_t &a = blocks[order[i - 1]], &b = blocks[order[i]];
+    if (a.offset + (int64_t)a.w * a.h > b.offset) return fail(ADJ_ERR_INVALID_ARG, "blocks %lld and %lld overlap", (long long)order[i - 1], (long long)order[i]);
+  }
+
+  // Tiles: blocks of one (w, h, tf_h, tf_v) class, filled in storage order.
+  struct Open {
+    std::vector<uint32_t> offs;
+    int64_t first;
+  };
+  std::unordered_map<uint64_t, Open> open;
+  struct Done {
+    int64_t first;
+    TileDev t;
+    std::vector<uint32_t> offs;
+  };
+  std::vector<Done> done;
+  auto emit = [&](uint64_t key, Open& o) {
+    Done d;
+    d.first = o.first;
+    d.t = TileDev{};
+    d.t.w = (uint16_t)(key >> 48);
+    d.t.h = (uint16_t)(key >> 32);
+    d.t.tf_h = (uint16_t)(key >> 16);
+    d.t.tf_v = (uint16_t)key;
+    d.t.nblk = (uint16_t)o.offs.size();
+    d.offs.swap(o.offs);
+    done.push_back(std::move(d));
+  };
+  for (int64_t i : order) {
+    const adj_block_t& b = blocks[i];
+    const uint64_t key = ((uint64_t)b.w << 48) | ((uint64_t)b.h << 32) | ((uint64_t)b.tf_h << 16) | b.tf_v;
+    Open& o = open[key];
+    if (o.offs.empty()) o.first = b.offset;
+    o.offs.push_back((uint32_t)(b.offset / 16));
+    if ((int)o.offs.size() >= tile_capacity(b.w, b.h)) emit(key, o);
+  }
+  for (auto& kv : open)
+    if (!kv.second.offs.empty()) emit(kv.first, kv.second);
+  std::stable_sort(done.begin(), done.end(), [](const Done& a, const Done& b) { return a.first < b.first; });
+  std::vector<TileDev> tiles;
+  std::vector<uint32_t> tblk;
+  tiles.reserve(done.size());
+  tblk.reserve(n_blocks);
+  for (Done& d : done) {
+    d.t.blk_begin = (uint32_t)tblk.size();
+    tiles.push_back(d.t);
+    tblk.insert(tblk.end(), d.offs.begin(), d.offs.end());
+  }
+
+  free_blocks(p);
+  if (!tiles.empty()) {
+    CUDA_TRY(cudaMalloc(&p->d_tiles, tiles.size() * sizeof(TileDev)));
+    CUDA_TRY(cudaMalloc(&p->d_tile_blk, tblk.size() * sizeof(uint32_t)));
+    CUDA_TRY(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p->d_tile_blk, tblk.data(), tblk.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  }
+  p->n_tiles = (int)tiles.size();
+  p->n_blocks = n_blocks;
+  p->total = total_coefs;
+  p->has_blocks = true;
+  return ADJ_OK;
+}
+
+int adj_transform_fwd(adj_plan_t* p, const int16_t* d_resid, float* d_coef, void* stream) {
+  g_err.clear();
+  return run(p, false, d_resid, d_coef, static_cast<cudaStream_t>(stream));
+}
+
+int adj_transform_inv(adj_plan_t* p, const float* d_coef, float* d_resid_out, void* stream) {
+  g_err.clear();
+  return run(p, true, d_coef, d_resid_out, static_cast<cudaStream_t>(stream));
+}
+
+int adj_transform_fwd_host(adj_plan_t* p, const int16_t* h_resid, float* h_coef, void* stream) {
+  g_err.clear();
+  return run_host(p, false, h_resid, h_coef, static_cast<cudaStream_t>(stream));
+}
+
+int adj_transform_inv_host(adj_plan_t* p, const float* h_coef, float* h_resid_out, void* stream) {
+  g_err.clear();
+  return run_host(p, true, h_coef, h_resid_out, static_cast<cudaStream_t>(stream));
+}
+
+int adj_plan_info(const adj_plan_t* p, adj_plan_info_t* info) {
+  g_err.clear();
+  if (!p || !info) return fail(ADJ_ERR_INVALID_ARG, "null argument");
+  info->n_blocks = p->n_blocks;
+  info->total_coefs = p->total;
+  info->n_tiles = p->n_tiles;
+  info->grid_fwd = p->grid_fwd;
+  info->grid_inv = p->grid_inv;
+  info->threads = p->threads;
+  info->smem_bytes = kSmemBytes;
+  info->n_sm = p->n_sm;
+  return ADJ_OK;
+}
+
+void adj_plan_destroy(adj_plan_t* p) {
+  if (!p) return;
+  free_blocks(p);
+  cudaFree(p->d_tfs);
+  cudaFree(p->d_params);
+  cudaFree(p->d_counter);
+  cudaFree(p->d_host_in);
+  cudaFree(p->d_host_out);
+  delete p;
+}
+
+}  // extern "C"

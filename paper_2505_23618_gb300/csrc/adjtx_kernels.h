@@ -1,0 +1,25 @@
+// Host-side declarations of the kernel launchers (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adjtx_layout.h"
+
+namespace adjtx {
+
+struct FusedArgs {
+  const TileDev* tiles;
+  const uint32_t* tile_blk;   // block offsets / 16, grouped per tile
+  const TfDev* tfs;
+  const float* params;
+  const void* in;             // int16 (forward) or FP32 (inverse)
+  float* out;
+  unsigned* counter;          // [0] next tile, [1] finished CTAs; zero between launches
+  int n_tiles;
+};
+
+const void* fused_kernel_ptr(bool inverse, int threads);
+cudaError_t launch_fused(bool inverse, int threads, int grid, const FusedArgs& args, cudaStream_t stream);
+
+}  // namespace adjtx
