@@ -140,6 +140,36 @@ int adj_transform_inv(adj_plan_t* plan, const float* d_coef, float* d_resid_out,
 int adj_transform_fwd_host(adj_plan_t* plan, const int16_t* h_resid, float* h_coef, void* stream);
 int adj_transform_inv_host(adj_plan_t* plan, const float* h_coef, float* h_resid_out, void* stream);
 
+/*
+ * Forward transform of a uniform batch that allocates nothing.
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory on their processing path: a real-time encoder that reserves all
+ * of its GPU memory at start-up and must not call cudaMalloc/cudaFree per frame (they
+ * can synchronise the device and stall the rest of the pipeline), or a plug-in inside a
+ * host framework that owns the device memory and offers plug-ins no allocator.
+ *
+ * Computes the same transform as adj_transform_fwd with the same fused kernel, for
+ * n_blocks blocks of tf_v->n rows x tf_h->n columns stored back to back (block b starts
+ * at sample b * w * h), all using tf_h horizontally and tf_v vertically.  d_resid (int16)
+ * and d_coef (FP32) are caller-owned device buffers, 16-B aligned.  Asynchronous on
+ * `stream` like adj_transform_fwd.
+ *
+ * Scratch: the work counter, the two transform records, their FP32 parameters and the
+ * tile list live in one static device array of ADJ_NOALLOC_SCRATCH_BYTES that every
+ * device loading the library holds until the process exits.  No cudaMalloc, cudaFree or
+ * other allocating routine is called.  The first call on a device (with that device
+ * current) looks up the array's device address once; make that first call before any
+ * stream capture.  Every call shares the array: it clears the work counter and rewrites
+ * the rest, and calls that overlap on the GPU (other streams or host threads) race on it,
+ * so the caller must serialise them.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE (also n_blocks > ADJ_NOALLOC_MAX_BLOCKS),
+ * PARAM_MISMATCH, MISALIGNED, CUDA.
+ */
+#define ADJ_NOALLOC_SCRATCH_BYTES (3u << 20)
+#define ADJ_NOALLOC_MAX_BLOCKS 131072
+int adj_transform_fwd_uniform_noalloc(const adj_1d_desc_t* tf_h, const adj_1d_desc_t* tf_v, int64_t n_blocks,
+                                      const int16_t* d_resid, float* d_coef, void* stream);
+
 /* Launch geometry and tile statistics of a plan (for benchmarks and tests). */
 typedef struct {
   int64_t n_blocks;

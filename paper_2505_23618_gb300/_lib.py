@@ -29,6 +29,7 @@ EXPORTED = (
     "adj_plan_create", "adj_plan_set_blocks", "adj_plan_update_params",
     "adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host",
     "adj_transform_inv_host", "adj_plan_info", "adj_plan_destroy", "adj_last_error",
+    "adj_transform_fwd_uniform_noalloc",
 )
 
 
@@ -67,6 +68,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for f in ("adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host", "adj_transform_inv_host"):
         getattr(lib, f).argtypes = [vp, vp, vp, vp]
     lib.adj_plan_info.argtypes = [vp, C.POINTER(AdjPlanInfo)]
+    lib.adj_transform_fwd_uniform_noalloc.argtypes = [C.POINTER(Adj1dDesc), C.POINTER(Adj1dDesc), i64, vp, vp, vp]
     lib.adj_plan_destroy.argtypes = [vp]
     lib.adj_plan_destroy.restype = None
     lib.adj_last_error.restype = C.c_char_p

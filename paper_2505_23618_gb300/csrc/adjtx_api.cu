@@ -251,6 +251,13 @@ extern "C" {
 
 const char* adj_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+// Lets other translation units of the library report errors through adj_last_error().
+void adjtx::set_last_error(const char* msg) { g_err = msg; }
+
+extern "C" {
+
 int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, int32_t flags) {
   g_err.clear();
   if (!plan) return fail(ADJ_ERR_INVALID_ARG, "null plan pointer");

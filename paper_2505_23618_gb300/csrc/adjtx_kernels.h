@@ -20,6 +20,7 @@ struct FusedArgs {
 };
 
 const void* fused_kernel_ptr(bool inverse, int threads);
+void set_last_error(const char* msg);
 cudaError_t launch_fused(bool inverse, int threads, int grid, const FusedArgs& args, cudaStream_t stream);
 
 }  // namespace adjtx
