@@ -328,3 +328,115 @@ def eq2_weighted_error(H, D) -> float:
     alpha = math.log(100.0) / N
     w = np.exp(-alpha * np.arange(N))[:, None]
     return float(np.sum(w * (H - D) ** 2))
+
+
+# --------------------------------------------------------------------------
+# Gradients (design of the adjustments, Eq. 2 and the Givens factorisation after
+# it; Section 2.2).  Everything is FP64 and follows the chain rule term by term.
+# --------------------------------------------------------------------------
+
+def grad_2d(X, G, Hh, Hv):
+    """For Y = H_v X H_h^T and upstream G = dL/dY (stacks (..., h, w)):
+    returns (dL/dX, dL/dH_h, dL/dH_v) with dL/dX = H_v^T G H_h,
+    dL/dH_h = sum_b G_b^T H_v X_b and dL/dH_v = sum_b G_b H_h X_b^T."""
+    X = np.asarray(X, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    gX = Hv.T @ G @ Hh
+    Xb = X.reshape((-1,) + X.shape[-2:])
+    Gb = G.reshape((-1,) + G.shape[-2:])
+    dHh = np.einsum("bji,jk,bkl->il", Gb, Hv, Xb)
+    dHv = np.einsum("bij,jk,blk->il", Gb, Hh, Xb)
+    return gX, dHh, dHv
+
+
+def grad_band_angles(N, core, parities, angles, dH):
+    """dL/dtheta for H = B G_{L-1} ... G_0 given dL/dH.
+
+    dL/dtheta_j = < dL/dH , B G_{L-1} .. G_{l+1} (dG_l/dtheta_j) G_{l-1} .. G_0 >,
+    where layer l holds rotation j and dG_l/dtheta_j is zero except for its 2x2 block
+    [[-s, -c], [c, -s]]."""
+    angles = np.asarray(angles, dtype=np.float64).ravel()
+    B = core_matrix(N, core)
+    layers, pos = [], 0
+    for p in parities:
+        cnt = len(layer_pairs(N, int(p)))
+        layers.append((int(p), angles[pos:pos + cnt]))
+        pos += cnt
+    Gs = [givens_layer(N, p, a) for p, a in layers]
+    out = np.zeros_like(angles)
+    pos = 0
+    for l, (p, a) in enumerate(layers):
+        left = B.copy()
+        for m in range(len(Gs) - 1, l, -1):
+            left = left @ Gs[m]
+        right = np.eye(N)
+        for m in range(l):
+            right = Gs[m] @ right
+        M = left.T @ dH @ right.T          # dL/dG_l
+        for q, ((i, j), th) in enumerate(zip(layer_pairs(N, p), a)):
+            c, s = math.cos(th), math.sin(th)
+            out[pos + q] = -s * M[i, i] - c * M[i, j] + c * M[j, i] - s * M[j, j]
+        pos += len(a)
+    return out
+
+
+def grad_post_q(N, core, K, dH):
+    """dL/dQ for H = diag(Q, I) B: the top-left K x K block of dL/dH B^T."""
+    B = core_matrix(N, core)
+    return (dH @ B.T)[:K, :K]
+
+
+def skew_from_params(w, K):
+    """K x K skew-symmetric W from its K(K-1)/2 upper-triangle entries (row major)."""
+    W = np.zeros((K, K))
+    iu = np.triu_indices(K, 1)
+    W[iu] = np.asarray(w, dtype=np.float64)
+    return W - W.T
+
+
+def cayley(w, K, D=None):
+    """Q = D (I + W)^{-1} (I - W): orthogonal with det = det(D) (D a fixed +-1 diagonal)."""
+    W = skew_from_params(w, K)
+    I = np.eye(K)
+    Q = np.linalg.solve(I + W, I - W)
+    if D is not None:
+        Q = np.diag(D) @ Q
+    return Q
+
+
+def cayley_grad(w, K, GQ, D=None):
+    """dL/dw for Q = D Cayley(W): with C = Cayley(W) and G_C = D^T dL/dQ,
+    dL/dW_full = -(I + W)^{-T} G_C (C + I)^T and dL/dw_ij = M_ij - M_ji (i < j)."""
+    W = skew_from_params(w, K)
+    I = np.eye(K)
+    C = np.linalg.solve(I + W, I - W)
+    GC = np.asarray(GQ, dtype=np.float64)
+    if D is not None:
+        GC = np.diag(D) @ GC
+    M = -np.linalg.solve((I + W).T, GC) @ (C + I).T
+    iu = np.triu_indices(K, 1)
+    return (M - M.T)[iu]
+
+
+def basis_loss(H, D, M):
+    """sum_{k<M} |h_k - d_k|^2 over the first M rows (basis vectors) and its dL/dH."""
+    H = np.asarray(H, dtype=np.float64)
+    diff = np.zeros_like(H)
+    diff[:M] = H[:M] - np.asarray(D, dtype=np.float64)[:M]
+    return float(np.sum(diff ** 2)), 2.0 * diff
+
+
+def proxy_loss(Y):
+    """Coding-gain proxy (1/(h w)) sum_{kv,kh} log(mean_b Y_b[kv,kh]^2) over a stack of
+    coefficient blocks, and its dL/dY."""
+    Y = np.asarray(Y, dtype=np.float64)
+    nb = Y.shape[0]
+    var = np.mean(Y ** 2, axis=0)
+    hw = Y.shape[1] * Y.shape[2]
+    L = float(np.sum(np.log(var)) / hw)
+    G = (2.0 / (hw * nb)) * Y / var[None]
+    return L, G
+
+
+__all__ += ["grad_2d", "grad_band_angles", "grad_post_q", "skew_from_params", "cayley",
+            "cayley_grad", "basis_loss", "proxy_loss"]
