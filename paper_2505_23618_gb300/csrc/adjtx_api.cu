@@ -67,7 +67,9 @@ struct adj_plan {
   TileDev* d_tiles = nullptr;
   uint32_t* d_tile_blk = nullptr;
   int n_tiles = 0;
-  unsigned* d_counter = nullptr;  // [0..1] forward, [2..3] inverse
+  SchedState* d_sched = nullptr;  // [0] forward, [1] inverse
+  unsigned* d_range_begin = nullptr;
+  int n_ranges = 0;
   int grid_fwd = 0, grid_inv = 0;
   void* d_host_in = nullptr;
   float* d_host_out = nullptr;
@@ -182,8 +184,11 @@ int upload_params(adj_plan* p) {
 void free_blocks(adj_plan* p) {
   cudaFree(p->d_tiles);
   cudaFree(p->d_tile_blk);
+  cudaFree(p->d_range_begin);
   p->d_tiles = nullptr;
   p->d_tile_blk = nullptr;
+  p->d_range_begin = nullptr;
+  p->n_ranges = 0;
   p->n_tiles = 0;
   p->has_blocks = false;
 }
@@ -207,8 +212,10 @@ int run(adj_plan* p, bool inverse, const void* in, float* out, cudaStream_t stre
   a.params = p->d_params;
   a.in = in;
   a.out = out;
-  a.counter = p->d_counter + (inverse ? 2 : 0);
+  a.sched = p->d_sched + (inverse ? 1 : 0);
+  a.range_begin = p->d_range_begin;
   a.n_tiles = p->n_tiles;
+  a.n_ranges = p->n_ranges;
   cudaError_t e = launch_fused(inverse, p->threads, inverse ? p->grid_inv : p->grid_fwd, a, stream);
   if (e != cudaSuccess) return cuda_fail(e, inverse ? "inverse launch" : "forward launch");
   return ADJ_OK;
@@ -279,9 +286,9 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
   }
   int rc = upload_params(p);
   if (!rc) {
-    e = cudaMalloc(&p->d_counter, 4 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(p->d_counter, 0, 4 * sizeof(unsigned));
-    if (e != cudaSuccess) rc = cuda_fail(e, "counter allocation");
+    e = cudaMalloc(&p->d_sched, 2 * sizeof(SchedState));
+    if (e == cudaSuccess) e = cudaMemset(p->d_sched, 0, 2 * sizeof(SchedState));
+    if (e != cudaSuccess) rc = cuda_fail(e, "scheduler state allocation");
   }
   for (int inv = 0; inv < 2 && !rc; ++inv) {
     const void* fn = fused_kernel_ptr(inv, p->threads);
@@ -343,13 +350,16 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
     if (a.offset + (int64_t)a.w * a.h > b.offset) return fail(ADJ_ERR_INVALID_ARG, "blocks %lld and %lld overlap", (long long)order[i - 1], (long long)order[i]);
   }
 
-  // Tiles: blocks of one (w, h, tf_h, tf_v) class, filled in storage order.
+  // Tiles: blocks of one (w, h, tf_h, tf_v) class, filled in storage order, then listed
+  // class by class so that consecutive tiles run the same code: the order is by block size,
+  // then by the code-determining (core, kind) of each direction, then by transform index.
   struct Open {
     std::vector<uint32_t> offs;
     int64_t first;
   };
   std::unordered_map<uint64_t, Open> open;
   struct Done {
+    uint64_t key;
     int64_t first;
     TileDev t;
     std::vector<uint32_t> offs;
@@ -357,6 +367,7 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
   std::vector<Done> done;
   auto emit = [&](uint64_t key, Open& o) {
     Done d;
+    d.key = key;
     d.first = o.first;
     d.t = TileDev{};
     d.t.w = (uint16_t)(key >> 48);
@@ -377,24 +388,56 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
   }
   for (auto& kv : open)
     if (!kv.second.offs.empty()) emit(kv.first, kv.second);
-  std::stable_sort(done.begin(), done.end(), [](const Done& a, const Done& b) { return a.first < b.first; });
+  auto code_key = [&](const Done& d) {
+    const TfHost &th = p->tfs[d.t.tf_h], &tv = p->tfs[d.t.tf_v];
+    return ((uint64_t)d.t.w << 40) | ((uint64_t)d.t.h << 32) | ((uint64_t)th.kind << 28) |
+           ((uint64_t)th.core << 24) | ((uint64_t)tv.kind << 20) | ((uint64_t)tv.core << 16);
+  };
+  std::stable_sort(done.begin(), done.end(), [&](const Done& a, const Done& b) {
+    const uint64_t ka = code_key(a), kb = code_key(b);
+    if (ka != kb) return ka < kb;
+    return a.key != b.key ? a.key < b.key : a.first < b.first;
+  });
   std::vector<TileDev> tiles;
   std::vector<uint32_t> tblk;
   tiles.reserve(done.size());
   tblk.reserve(n_blocks);
+  // Each tile's block list starts on a 16-byte boundary and the list ends with 4 spare
+  // entries: the kernel fetches a tile's offsets with 16-byte asynchronous copies.
   for (Done& d : done) {
+    while (tblk.size() % 4) tblk.push_back(0u);
     d.t.blk_begin = (uint32_t)tblk.size();
     tiles.push_back(d.t);
     tblk.insert(tblk.end(), d.offs.begin(), d.offs.end());
+  }
+  tblk.resize(tblk.size() + 4, 0u);
+
+  // Per-SM ranges of the sorted tile list with about equal numbers of coefficients.
+  const int n_ranges = tiles.empty() ? 0 : (int)std::min<size_t>({(size_t)std::max(1, p->n_sm), (size_t)kMaxRanges, tiles.size()});
+  std::vector<unsigned> rbeg;
+  if (n_ranges > 0) {
+    std::vector<int64_t> cum(tiles.size() + 1, 0);
+    for (size_t i = 0; i < tiles.size(); ++i) cum[i + 1] = cum[i] + (int64_t)tiles[i].nblk * tiles[i].w * tiles[i].h;
+    rbeg.push_back(0);
+    for (int r = 1; r < n_ranges; ++r) {
+      const int64_t target = cum.back() * r / n_ranges;
+      size_t i = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
+      i = std::max<size_t>(i, rbeg.back());
+      rbeg.push_back((unsigned)std::min(i, tiles.size()));
+    }
+    rbeg.push_back((unsigned)tiles.size());
   }
 
   free_blocks(p);
   if (!tiles.empty()) {
     CUDA_TRY(cudaMalloc(&p->d_tiles, tiles.size() * sizeof(TileDev)));
     CUDA_TRY(cudaMalloc(&p->d_tile_blk, tblk.size() * sizeof(uint32_t)));
+    CUDA_TRY(cudaMalloc(&p->d_range_begin, rbeg.size() * sizeof(unsigned)));
     CUDA_TRY(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(p->d_tile_blk, tblk.data(), tblk.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p->d_range_begin, rbeg.data(), rbeg.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
   }
+  p->n_ranges = n_ranges;
   p->n_tiles = (int)tiles.size();
   p->n_blocks = n_blocks;
   p->total = total_coefs;
@@ -441,7 +484,7 @@ void adj_plan_destroy(adj_plan_t* p) {
   free_blocks(p);
   cudaFree(p->d_tfs);
   cudaFree(p->d_params);
-  cudaFree(p->d_counter);
+  cudaFree(p->d_sched);
   cudaFree(p->d_host_in);
   cudaFree(p->d_host_out);
   delete p;

@@ -84,52 +84,63 @@ __device__ __forceinline__ void band(float (&v)[N], const TfDev& tf, const float
 // directly at runtime index i (four rows per step, independent accumulators).
 // Inverse (C^T): u_j = sum_i Qp[i][j] y_i with y_i read back from the source line.
 // ---------------------------------------------------------------------------------
+// Rows of Qp handled per step: enough independent accumulators for ILP while the Q
+// loads the compiler hoists out of the unrolled dot product still fit in registers.
+template <int KT>
+struct PostRows {
+  static constexpr int R = KT >= 64 ? 1 : (KT >= 32 ? 2 : 4);
+};
+
 template <int N, int KT, class Dst>
 __device__ __forceinline__ void post_fwd_k(const float (&v)[N], const float* __restrict__ Q,
                                            const Dst& dst) {
+  constexpr int R = PostRows<KT>::R;
 #pragma unroll
   for (int i = KT; i < N; ++i) dst.put(i, v[i]);
 #pragma unroll 1
-  for (int i = 0; i < KT; i += 4) {
+  for (int i = 0; i < KT; i += R) {
     const float4* q = reinterpret_cast<const float4*>(Q + i * KT);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.f;
 #pragma unroll
     for (int j = 0; j < KT / 4; ++j) {
-      const float4 c0 = __ldg(q + j);
-      const float4 c1 = __ldg(q + KT / 4 + j);
-      const float4 c2 = __ldg(q + 2 * (KT / 4) + j);
-      const float4 c3 = __ldg(q + 3 * (KT / 4) + j);
       const float u0 = v[4 * j], u1 = v[4 * j + 1], u2 = v[4 * j + 2], u3 = v[4 * j + 3];
-      a0 = fmaf(c0.x, u0, a0); a0 = fmaf(c0.y, u1, a0); a0 = fmaf(c0.z, u2, a0); a0 = fmaf(c0.w, u3, a0);
-      a1 = fmaf(c1.x, u0, a1); a1 = fmaf(c1.y, u1, a1); a1 = fmaf(c1.z, u2, a1); a1 = fmaf(c1.w, u3, a1);
-      a2 = fmaf(c2.x, u0, a2); a2 = fmaf(c2.y, u1, a2); a2 = fmaf(c2.z, u2, a2); a2 = fmaf(c2.w, u3, a2);
-      a3 = fmaf(c3.x, u0, a3); a3 = fmaf(c3.y, u1, a3); a3 = fmaf(c3.z, u2, a3); a3 = fmaf(c3.w, u3, a3);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float4 c = __ldg(q + r * (KT / 4) + j);
+        acc[r] = fmaf(c.x, u0, acc[r]);
+        acc[r] = fmaf(c.y, u1, acc[r]);
+        acc[r] = fmaf(c.z, u2, acc[r]);
+        acc[r] = fmaf(c.w, u3, acc[r]);
+      }
     }
-    dst.put_rt(i, a0);
-    dst.put_rt(i + 1, a1);
-    dst.put_rt(i + 2, a2);
-    dst.put_rt(i + 3, a3);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst.put_rt(i + r, acc[r]);
   }
 }
 
 template <int N, int KT, class Src>
 __device__ __forceinline__ void post_inv_k(float (&v)[N], const float* __restrict__ Q, const Src& src) {
+  constexpr int R = PostRows<KT>::R;
 #pragma unroll
   for (int j = 0; j < KT; ++j) v[j] = 0.f;
 #pragma unroll 1
-  for (int i = 0; i < KT; i += 4) {
-    const float y0 = src.get_rt(i), y1 = src.get_rt(i + 1), y2 = src.get_rt(i + 2), y3 = src.get_rt(i + 3);
+  for (int i = 0; i < KT; i += R) {
+    float y[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) y[r] = src.get_rt(i + r);
     const float4* q = reinterpret_cast<const float4*>(Q + i * KT);
 #pragma unroll
     for (int j = 0; j < KT / 4; ++j) {
-      const float4 c0 = __ldg(q + j);
-      const float4 c1 = __ldg(q + KT / 4 + j);
-      const float4 c2 = __ldg(q + 2 * (KT / 4) + j);
-      const float4 c3 = __ldg(q + 3 * (KT / 4) + j);
-      v[4 * j] = fmaf(c3.x, y3, fmaf(c2.x, y2, fmaf(c1.x, y1, fmaf(c0.x, y0, v[4 * j]))));
-      v[4 * j + 1] = fmaf(c3.y, y3, fmaf(c2.y, y2, fmaf(c1.y, y1, fmaf(c0.y, y0, v[4 * j + 1]))));
-      v[4 * j + 2] = fmaf(c3.z, y3, fmaf(c2.z, y2, fmaf(c1.z, y1, fmaf(c0.z, y0, v[4 * j + 2]))));
-      v[4 * j + 3] = fmaf(c3.w, y3, fmaf(c2.w, y2, fmaf(c1.w, y1, fmaf(c0.w, y0, v[4 * j + 3]))));
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float4 c = __ldg(q + r * (KT / 4) + j);
+        v[4 * j] = fmaf(c.x, y[r], v[4 * j]);
+        v[4 * j + 1] = fmaf(c.y, y[r], v[4 * j + 1]);
+        v[4 * j + 2] = fmaf(c.z, y[r], v[4 * j + 2]);
+        v[4 * j + 3] = fmaf(c.w, y[r], v[4 * j + 3]);
+      }
     }
   }
 }
@@ -164,11 +175,15 @@ __device__ __forceinline__ void post_inv(float (&v)[N], const TfDev& tf, const f
 // Line accessors.
 // ---------------------------------------------------------------------------------
 
-// A staged int16 row in shared memory (16-B aligned when the row is 16 B or longer).
-struct SrcRowI16 {
-  const int16_t* p;
+// One row of a swizzled tile buffer, transformed in place by the thread that owns it.
+// The staged input of the row (int16 forward, FP32 inverse) sits in the row's own region:
+// int16 chunk q (8 samples) and FP32 chunk q (4 samples) are both at chunk slot q ^ f.
+struct RowSw {
+  float* p;  // row start
+  int f;     // swizzle of this row
+  __device__ __forceinline__ int at(int i) const { return ((((i >> 2) ^ f)) << 2) + (i & 3); }
   template <int N>
-  __device__ __forceinline__ void load(float (&v)[N]) const {
+  __device__ __forceinline__ void load_i16(float (&v)[N]) const {
     if constexpr (N == 4) {
       const int2 r = *reinterpret_cast<const int2*>(p);
       v[0] = (float)(int16_t)(r.x & 0xffff); v[1] = (float)(r.x >> 16);
@@ -176,7 +191,7 @@ struct SrcRowI16 {
     } else {
 #pragma unroll
       for (int q = 0; q < N / 8; ++q) {
-        const int4 r = reinterpret_cast<const int4*>(p)[q];
+        const int4 r = *reinterpret_cast<const int4*>(p + ((q ^ f) << 2));
         v[8 * q + 0] = (float)(int16_t)(r.x & 0xffff); v[8 * q + 1] = (float)(r.x >> 16);
         v[8 * q + 2] = (float)(int16_t)(r.y & 0xffff); v[8 * q + 3] = (float)(r.y >> 16);
         v[8 * q + 4] = (float)(int16_t)(r.z & 0xffff); v[8 * q + 5] = (float)(r.z >> 16);
@@ -184,68 +199,73 @@ struct SrcRowI16 {
       }
     }
   }
-  __device__ __forceinline__ float get_rt(int i) const { return (float)p[i]; }
-};
-
-// A staged FP32 row in shared memory (16-B aligned).
-struct SrcRowF32 {
-  const float* p;
   template <int N>
   __device__ __forceinline__ void load(float (&v)[N]) const {
 #pragma unroll
     for (int q = 0; q < N / 4; ++q) {
-      const float4 r = reinterpret_cast<const float4*>(p)[q];
+      const float4 r = *reinterpret_cast<const float4*>(p + ((q ^ f) << 2));
       v[4 * q] = r.x; v[4 * q + 1] = r.y; v[4 * q + 2] = r.z; v[4 * q + 3] = r.w;
     }
   }
-  __device__ __forceinline__ float get_rt(int i) const { return p[i]; }
-};
-
-// A row of the transpose buffer T.
-struct DstTRow {
-  float* p;
-  __device__ __forceinline__ void put(int i, float x) const { p[i] = x; }
-  __device__ __forceinline__ void put_rt(int i, float x) const { p[i] = x; }
+  __device__ __forceinline__ float get_rt(int i) const { return p[at(i)]; }
+  __device__ __forceinline__ void put(int i, float x) const { p[at(i)] = x; }
+  __device__ __forceinline__ void put_rt(int i, float x) const { p[at(i)] = x; }
   template <int N>
   __device__ __forceinline__ void store(const float (&v)[N]) const {
 #pragma unroll
-    for (int i = 0; i < N; ++i) p[i] = v[i];
+    for (int q = 0; q < N / 4; ++q)
+      *reinterpret_cast<float4*>(p + ((q ^ f) << 2)) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   }
 };
 
-// A column of T (element i at p[i * s]).
-struct SrcTCol {
-  const float* p;
-  int s;
+// Column c of a w = W wide block in a swizzled tile buffer.  Element i sits at
+// i*W + (((c >> 2) ^ f(i)) << 2) + (c & 3); f(i) takes at most 8 values, so one base
+// pointer per value keeps every access a shared load with an immediate offset.
+template <int W>
+struct ColSw {
+  static constexpr int SH = sw_shift(W), MK = sw_mask(W), NK = MK + 1;
+  const float* p[NK];
+  const float* blk;
+  int c;
+  __device__ __forceinline__ ColSw(const float* block, int col) : blk(block), c(col) {
+#pragma unroll
+    for (int k = 0; k < NK; ++k) p[k] = block + ((((col >> 2) ^ k)) << 2) + (col & 3);
+  }
   template <int N>
   __device__ __forceinline__ void load(float (&v)[N]) const {
 #pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = p[i * s];
+    for (int i = 0; i < N; ++i) v[i] = p[(i >> SH) & MK][i * W];
   }
-  __device__ __forceinline__ float get_rt(int i) const { return p[i * s]; }
+  __device__ __forceinline__ float get_rt(int i) const {
+    return blk[i * W + ((((c >> 2) ^ ((i >> SH) & MK))) << 2) + (c & 3)];
+  }
 };
 
-// A column of an output block in global memory (element i at p[i * s]).
+// A column of an output block in global memory (element i at p[i * S]).
+template <int S>
 struct DstGCol {
   float* p;
-  int s;
-  __device__ __forceinline__ void put(int i, float x) const { p[i * s] = x; }
-  __device__ __forceinline__ void put_rt(int i, float x) const { p[i * s] = x; }
+  __device__ __forceinline__ void put(int i, float x) const { p[i * S] = x; }
+  __device__ __forceinline__ void put_rt(int i, float x) const { p[i * S] = x; }
   template <int N>
   __device__ __forceinline__ void store(const float (&v)[N]) const {
 #pragma unroll
-    for (int i = 0; i < N; ++i) p[i * s] = v[i];
+    for (int i = 0; i < N; ++i) p[i * S] = v[i];
   }
 };
 
 // ---------------------------------------------------------------------------------
 // One line of a pass.  Forward: A (band), B (core), C (post).  Inverse: C^T, B^T, A^T.
 // ---------------------------------------------------------------------------------
-template <int N, bool INV, class Src, class Dst>
+template <int N, bool INV, bool I16, class Src, class Dst>
 __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __restrict__ P,
                                                const Src& src, const Dst& dst) {
   float v[N];
-  src.template load<N>(v);
+  if constexpr (I16) {
+    src.template load_i16<N>(v);
+  } else {
+    src.template load<N>(v);
+  }
   if (!INV) {
     if (tf.kind == KIND_BAND) band<N, false>(v, tf, P);
     core_apply<N>(tf.core, v);
@@ -270,6 +290,70 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ unsigned sm_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// Completes a claim whose atomicAdd on s->pos[range] returned k (issued earlier, so its
+// latency overlapped other work): the tile index, or the result of a full search when
+// the range turned out to be exhausted.
+__device__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges, int& range);
+__device__ __forceinline__ int claim_resolve(SchedState* s, const unsigned* __restrict__ begin, int n_ranges,
+                                             int& range, unsigned k) {
+  const unsigned t = __ldg(begin + range) + k;
+  if (t < __ldg(begin + range + 1)) return (int)t;
+  return grab_tile(s, begin, n_ranges, range);
+}
+
+// First range after `from` (cyclically) whose bit is clear in the bitmap snapshot, or -1.
+__device__ __forceinline__ int next_open_range(const unsigned* ex, int from, int n_ranges) {
+  for (int step = 1; step <= n_ranges; ++step) {
+    const int r = (from + step) % n_ranges;
+    if (!((ex[r >> 5] >> (r & 31)) & 1u)) return r;
+  }
+  return -1;
+}
+
+// Next tile for this CTA (called by one thread), or -1 when every tile is claimed.
+// `range` is the CTA's current range (initially -1: start at the SM's own range).
+// Every probe either returns a tile or marks one more range exhausted, so the loop ends
+// after at most 2 * n_ranges + 2 probes.
+__device__ __noinline__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges,
+                                       int& range) {
+  if (range < 0) range = (int)(sm_id() % (unsigned)n_ranges);
+  unsigned ex[kMaxRanges / 32];
+  bool have = false;
+  for (int probes = 0; probes < 2 * n_ranges + 2; ++probes) {
+    const unsigned k = atomicAdd(&s->pos[range], 1u);
+    const unsigned t = __ldg(begin + range) + k;
+    if (t < __ldg(begin + range + 1)) return (int)t;
+    atomicOr(&s->exhausted[range >> 5], 1u << (range & 31));
+    if (!have) {
+      const volatile unsigned* g = s->exhausted;
+      for (int i = 0; i < (n_ranges + 31) / 32; ++i) ex[i] = g[i];
+      have = true;
+    }
+    ex[range >> 5] |= 1u << (range & 31);
+    int next = next_open_range(ex, range, n_ranges);
+    if (next < 0) {
+      // the snapshot says everything is taken: confirm with a fresh one
+      const volatile unsigned* g = s->exhausted;
+      for (int i = 0; i < (n_ranges + 31) / 32; ++i) ex[i] = g[i];
+      next = next_open_range(ex, range, n_ranges);
+      if (next < 0) return -1;
+    }
+    range = next;
+  }
+  return -1;
+}
 
 }  // namespace adjtx

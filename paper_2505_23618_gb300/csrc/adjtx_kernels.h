@@ -15,8 +15,10 @@ struct FusedArgs {
   const float* params;
   const void* in;             // int16 (forward) or FP32 (inverse)
   float* out;
-  unsigned* counter;          // [0] next tile, [1] finished CTAs; zero between launches
+  SchedState* sched;          // zero between launches
+  const unsigned* range_begin;  // n_ranges + 1 tile indices
   int n_tiles;
+  int n_ranges;
 };
 
 const void* fused_kernel_ptr(bool inverse, int threads);

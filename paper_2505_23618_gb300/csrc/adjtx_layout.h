@@ -5,9 +5,9 @@
 #include <stdint.h>
 
 #if defined(__CUDACC__)
-#define ADJ_HD __host__ __device__ __forceinline__
+#define ADJ_HD __host__ __device__ __forceinline__ constexpr
 #else
-#define ADJ_HD inline
+#define ADJ_HD constexpr inline
 #endif
 
 namespace adjtx {
@@ -37,12 +37,30 @@ struct TileDev {
 };
 static_assert(sizeof(TileDev) == 16, "TileDev layout");
 
-// Shared-memory budgets of one CTA: the transpose buffer T (FP32) and the staging
-// buffer of the input tile (int16 forward, FP32 inverse).  One 64x64 block fills both.
-constexpr int kTBytes = 4 * 64 * 65;        // 16640
-constexpr int kStgBytes = 64 * (4 * 64 + 16);  // 17408
-constexpr int kSmemBytes = kTBytes + kStgBytes;
+// Shared memory of one CTA: two tile buffers (the tile being transformed and the next
+// tile being loaded).  A tile holds at most kTileCoefs coefficients as FP32; the staged
+// input of each row (int16 forward, FP32 inverse) sits inside that row's own region, so
+// the row pass transforms it in place.
+constexpr int kTileCoefs = 4096;
+constexpr int kBufBytes = 4 * kTileCoefs;
+constexpr int kSmemBytes = 2 * kBufBytes;
 constexpr int kMaxTileBlocks = 256;
+
+// Work distribution.  The tile list is sorted by class, so consecutive tiles share
+// (w, h, core, adjustment) and therefore code.  The planner cuts the list into kRanges
+// contiguous ranges of about equal work; the CTAs of SM s take tiles from range
+// s mod n_ranges in order, so each SM walks through neighbouring classes and keeps its
+// instruction cache warm.  A CTA whose range is empty marks it in the exhausted bitmap
+// and moves on to the next range that is not marked (work stealing); the bitmap keeps
+// that search O(1) per range.  All words are zero between launches (the last CTA of a
+// launch clears them).
+constexpr int kMaxRanges = 256;
+struct SchedState {
+  unsigned pos[kMaxRanges];        // tiles taken from each range
+  unsigned exhausted[kMaxRanges / 32];
+  unsigned done;                   // CTAs finished
+  unsigned pad[7];
+};
 
 ADJ_HD int ilog2(int x) {
   int r = 0;
@@ -50,26 +68,22 @@ ADJ_HD int ilog2(int x) {
   return r;
 }
 
-// Staging row stride in bytes: rows of 16 B or less are packed; longer rows get 16 B
-// of padding so that 8 consecutive rows read with 16-B loads hit 8 distinct bank groups.
-ADJ_HD int stg_row_bytes(int w, int esz) {
-  const int rb = w * esz;
-  return rb <= 16 ? rb : rb + 16;
+// Tile buffer layout.  Block b of a tile starts at float b*w*h; row r of a block is w
+// floats (w/4 chunks of 16 B) at r*w.  Chunk q of row r is stored at chunk slot q ^ f(r):
+// 8 consecutive rows read or written with 16-B accesses then touch 8 distinct bank groups,
+// and 32 consecutive columns of one row fall in 32 distinct banks.
+ADJ_HD int sw_shift(int w) {
+  const int lg = ilog2(w / 4);
+  return lg >= 3 ? 0 : 3 - lg;
 }
-ADJ_HD int stg_block_bytes(int w, int h, int esz) { return h * stg_row_bytes(w, esz); }
+ADJ_HD int sw_mask(int w) { return (w / 4 < 8 ? w / 4 : 8) - 1; }
+ADJ_HD int sw_f(int r, int w) { return (r >> sw_shift(w)) & sw_mask(w); }
+// float index of element (r, c) inside a block of width w
+ADJ_HD int sw_index(int r, int c, int w) { return r * w + ((((c >> 2) ^ sw_f(r, w))) << 2) + (c & 3); }
 
-// T: each block row has w+1 floats (odd stride -> row-pass stores conflict-free);
-// tall narrow blocks get w floats of block padding so that the blocks sharing a warp in
-// the column pass fall into different bank windows.
-ADJ_HD int t_block_floats(int w, int h) {
-  return h * (w + 1) + ((w < 32 && h > w) ? w : 0);
-}
-
-// Largest number of blocks of size w x h that one tile can hold.
+// Largest number of w x h blocks in one tile.
 ADJ_HD int tile_capacity(int w, int h) {
-  int a = kTBytes / (4 * t_block_floats(w, h));
-  int b = kStgBytes / stg_block_bytes(w, h, 4);
-  int c = a < b ? a : b;
+  const int c = kTileCoefs / (w * h);
   return c < kMaxTileBlocks ? c : kMaxTileBlocks;
 }
 

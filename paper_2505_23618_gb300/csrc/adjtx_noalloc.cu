@@ -14,7 +14,7 @@
 // held until the process exits.  Its device address is taken once per device with
 // cudaGetSymbolAddress, on the first call made while that device is current.  All calls
 // share the array and it keeps the previous call's contents; each call clears the work
-// counter and rewrites everything else it reads.  Calls that overlap on the GPU (two
+// scheduling state and rewrites everything else it reads.  Calls that overlap on the GPU (two
 // streams, or two host threads) race on the array and must be serialised by the caller.
 #include <cuda_runtime.h>
 
@@ -32,9 +32,10 @@ using namespace adjtx;
 namespace {
 
 constexpr size_t kScratchBytes = ADJ_NOALLOC_SCRATCH_BYTES;
-constexpr size_t kCounterOff = 0;                      // 4 words
-constexpr size_t kTfOff = 256;                         // 2 TfDev records
-constexpr size_t kParamOff = 512;                      // FP32 parameters
+constexpr size_t kSchedOff = 0;                                     // SchedState
+constexpr size_t kRangeOff = ((sizeof(SchedState) + 255) / 256) * 256;  // {0, n_tiles}
+constexpr size_t kTfOff = kRangeOff + 256;                           // 2 TfDev records
+constexpr size_t kParamOff = kTfOff + 256;                            // FP32 parameters
 // A transform carries a band (at most 64 layers x 32 pairs x (cos, sin)) or a post block
 // (at most 64 x 64), never both: 4096 floats each, plus alignment padding.
 constexpr size_t kMaxParamFloats = 2 * 4096 + 16;
@@ -42,7 +43,9 @@ constexpr size_t kTileOff = kParamOff + ((kMaxParamFloats * 4 + 255) / 256) * 25
 constexpr size_t kTileBytes = (size_t)ADJ_NOALLOC_MAX_BLOCKS * sizeof(TileDev);
 constexpr size_t kBlkOff = kTileOff + kTileBytes;
 constexpr size_t kScratchNeed = kBlkOff + (size_t)ADJ_NOALLOC_MAX_BLOCKS * sizeof(uint32_t);
-static_assert(kScratchNeed <= kScratchBytes, "scratch layout exceeds the static array");
+// (+16: the kernel copies a tile's offsets from the 16-byte aligned address below the
+// list and up to 3 entries past it)
+static_assert(kScratchNeed + 16 <= kScratchBytes, "scratch layout exceeds the static array");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -205,11 +208,14 @@ extern "C" int adj_transform_fwd_uniform_noalloc(const adj_1d_desc_t* tf_h, cons
   const int cap = tile_capacity(w, h);
   const int nb = (int)n_blocks;
   const int n_tiles = (nb + cap - 1) / cap;
-  unsigned* counter = reinterpret_cast<unsigned*>(base + kCounterOff);
+  SchedState* sched = reinterpret_cast<SchedState*>(base + kSchedOff);
   TileDev* tiles = reinterpret_cast<TileDev*>(base + kTileOff);
   uint32_t* blk = reinterpret_cast<uint32_t*>(base + kBlkOff);
 
-  e = cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned), stream);
+  unsigned* range_begin = reinterpret_cast<unsigned*>(base + kRangeOff);
+  const unsigned ranges[2] = {0u, (unsigned)n_tiles};
+  e = cudaMemsetAsync(sched, 0, sizeof(SchedState), stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(range_begin, ranges, sizeof ranges, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(base + kTfOff, recs, sizeof recs, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(base + kParamOff, params, np * sizeof(float), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return cuda_err(e, "no-alloc upload");
@@ -227,8 +233,10 @@ extern "C" int adj_transform_fwd_uniform_noalloc(const adj_1d_desc_t* tf_h, cons
   a.params = reinterpret_cast<const float*>(base + kParamOff);
   a.in = d_resid;
   a.out = d_coef;
-  a.counter = counter;
+  a.sched = sched;
+  a.range_begin = range_begin;
   a.n_tiles = n_tiles;
+  a.n_ranges = 1;
   e = launch_fused(false, kThreads, grid, a, stream);
   if (e != cudaSuccess) return cuda_err(e, "no-alloc forward launch");
   return ADJ_OK;

@@ -117,10 +117,9 @@ def test_tile_capacity_boundaries(w, h):
 
 
 def _tile_capacity(w, h):
-    # mirror of the planner's rule (smem budgets), used only to pick boundary counts
-    tb = h * (w + 1) + (w if (w < 32 and h > w) else 0)
-    rs = 4 * w if 4 * w <= 16 else 4 * w + 16
-    return min((4 * 64 * 65) // (4 * tb), (64 * (4 * 64 + 16)) // (h * rs), 256)
+    # mirror of the planner's rule (4096 coefficients, at most 256 blocks per tile), used
+    # only to pick boundary counts
+    return min(4096 // (w * h), 256)
 
 
 def test_unsorted_blocks_with_gaps_untouched_elsewhere():
