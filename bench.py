@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Gcoef/s fwd+inv adjusted 2-D transforms (mixed 4-64)"
+METRIC = "Gcoef/s fwd+inv adjusted 2-D transforms (mixed 4-64) vs plain; % HBM roofline"
 UNIT = "Gcoef/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
@@ -268,6 +268,37 @@ def run_fused(args):
         t_total = float(tt.item())
     value = coefs * world * args.steps / t_total / 1e9
 
+    # the plain (unfused) form on the same blocks, replayed from CUDA graphs (its best case:
+    # no per-launch host overhead); same flushes and event timing as the fused kernels
+    from paper_2505_23618_gb300 import _lib as L
+    yp = torch.empty_like(y)
+    xrp = torch.empty_like(xr)
+    g_fwd = plan.graph(L.GRAPH_FWD_PLAIN, x, yp)
+    g_inv = plan.graph(L.GRAPH_INV_PLAIN, yp, xrp)
+    plain_steps = max(3, min(args.steps, 30))
+    for _ in range(2):
+        g_fwd.launch(stream)
+        g_inv.launch(stream)
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(plain_steps)]
+    for k in range(plain_steps):
+        flush.fill_(3.0)
+        pev[k][0].record(stream)
+        g_fwd.launch(stream)
+        pev[k][1].record(stream)
+        flush.fill_(4.0)
+        pev[k][2].record(stream)
+        g_inv.launch(stream)
+        pev[k][3].record(stream)
+    torch.cuda.synchronize()
+    pf = np.array([e[0].elapsed_time(e[1]) for e in pev]) * 1e-3
+    pi = np.array([e[2].elapsed_time(e[3]) for e in pev]) * 1e-3
+    plain_value = coefs * world / float(np.median(pf) + np.median(pi)) / 1e9
+    plain_launches = 6 * len(set(zip(wl.blocks["w"].tolist(), wl.blocks["h"].tolist())))
+    plain_rt = float((xrp - x.float()).abs().max())
+    g_fwd.close()
+    g_inv.close()
+    del yp, xrp
+
     # end to end through the host-buffer C-ABI calls (pinned memory), copies included
     h_x = torch.from_numpy(wl.data).pin_memory()
     h_y = torch.empty(coefs, dtype=torch.float32).pin_memory()
@@ -315,6 +346,11 @@ def run_fused(args):
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": coefs * (2 + 4),
                     "d2h_bytes_per_step": coefs * (4 + 4)},
             "gpu_launches": 2 * args.steps,
+            "vs_plain": round(value / plain_value, 3),
+            "plain": {"value": round(plain_value, 3), "unit": UNIT, "fwd_ms": round(float(np.median(pf)) * 1e3, 4),
+                      "inv_ms": round(float(np.median(pi)) * 1e3, 4), "launches_per_direction": plain_launches,
+                      "timed_steps": plain_steps, "how": "CUDA-graph replay of one launch per block size and step",
+                      "roundtrip_max_abs_err": plain_rt},
             "roofline": roof,
             "kernels": {k: {"ms": round(v["ms"], 4), "GB/s": round(v["gbs"], 1), "frac": round(v["frac"], 4)}
                         for k, v in kern.items()},

@@ -59,8 +59,11 @@ enum {
 
 /* Core B (Section 2.1). */
 typedef enum { ADJ_CORE_DCT2 = 0, ADJ_CORE_DCT3 = 1, ADJ_CORE_DST2 = 2, ADJ_CORE_DST3 = 3 } adj_core_t;
-/* Adjustment (Section 2.2): none, band pre-adjustment A, or top-left post-adjustment C. */
-typedef enum { ADJ_ADJ_NONE = 0, ADJ_ADJ_PRE_BAND = 1, ADJ_ADJ_POST_BLOCK = 2 } adj_kind_t;
+/* Adjustment (Section 2.2): none, band pre-adjustment A, or top-left post-adjustment C.
+ * ADJ_ADJ_DENSE is the reference the adjustments approximate: the 1-D transform is the given
+ * dense orthogonal n x n matrix (q, k = n; e.g. the exact DST-7 or DCT-8 of Section 2.2,
+ * Eq. 3) applied by a full matrix-vector product, with no fast core. */
+typedef enum { ADJ_ADJ_NONE = 0, ADJ_ADJ_PRE_BAND = 1, ADJ_ADJ_POST_BLOCK = 2, ADJ_ADJ_DENSE = 3 } adj_kind_t;
 
 #define ADJ_MAX_LAYERS 64
 
@@ -74,8 +77,8 @@ typedef struct {
   const uint8_t* layer_parity;  /* band: n_layers entries, 0 = even pairs, 1 = odd pairs */
   const double* angles;         /* band: angles of layer 0 first; n/2 per even layer,
                                    n/2 - 1 per odd layer */
-  int32_t k;                    /* post: size K of Q, 1 <= K <= n */
-  const double* q;              /* post: K x K row-major, orthogonal to 1e-6 */
+  int32_t k;                    /* post: size K of Q, 1 <= K <= n; dense: k = n */
+  const double* q;              /* post / dense: K x K row-major, orthogonal to 1e-6 */
 } adj_1d_desc_t;
 
 /* One residual block: h rows x w columns, row-major, starting at element `offset` of
@@ -133,6 +136,37 @@ int adj_transform_fwd(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, v
 int adj_transform_inv(adj_plan_t* plan, const float* d_coef, float* d_resid_out, void* stream);
 
 /*
+ * Backward of adj_transform_fwd for fitting the adjustments (the paper designs them by a
+ * constrained least-squares fit, Eq. 2, through the Givens factorisation after it).
+ * Given the forward input d_x (int16 or FP32 per x_dtype, device, the same layout) and
+ * d_gy = dL/dY (FP32, device), writes
+ *   d_gx      (optional, FP32, device, total_coefs): dL/dX = H_v^T G H_h per block;
+ *   d_gparams (optional, FP32, device): the gradients of every transform's parameters,
+ *             transform i at offsets[i] (adj_plan_param_layout): band -> one entry per angle
+ *             (same order as the angles), post -> K x K entries of dL/dQ (row major),
+ *             dense -> n x n entries, none -> nothing.
+ * Sums over blocks are formed per CTA in a fixed assignment and added in a fixed order, so
+ * repeated calls give bit-identical gradients.  Asynchronous on `stream`.
+ */
+#define ADJ_DTYPE_INT16 0
+#define ADJ_DTYPE_FP32 1
+int adj_transform_bwd(adj_plan_t* plan, const void* d_x, int32_t x_dtype, const float* d_gy, float* d_gx,
+                      float* d_gparams, void* stream);
+/* offsets[i] = first gradient entry of transform i; offsets[n_tfs] = total (n_tfs + 1 entries). */
+int adj_plan_param_layout(const adj_plan_t* plan, int32_t* offsets);
+
+/*
+ * Plain (unfused) form of the same transforms, the baseline the fused path is measured
+ * against: for every block size present, one launch per step of the chain (band, core,
+ * post) along the rows, then along the columns (forward; the inverse runs the transposed
+ * steps in reverse order), each step reading and writing FP32 lines in global memory.
+ * Same arguments, layout and results (up to FP32 rounding) as adj_transform_fwd/_inv;
+ * up to 150 launches per call.
+ */
+int adj_transform_fwd_plain(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, void* stream);
+int adj_transform_inv_plain(adj_plan_t* plan, const float* d_coef, float* d_resid_out, void* stream);
+
+/*
  * Host-buffer variants: copy the input from host memory to plan-owned device staging
  * buffers, transform, copy the result back and wait for it.  Page-locked host memory
  * gives full copy bandwidth.  The staging buffers are allocated on the first call.
@@ -169,6 +203,24 @@ int adj_transform_inv_host(adj_plan_t* plan, const float* h_coef, float* h_resid
 #define ADJ_NOALLOC_MAX_BLOCKS 131072
 int adj_transform_fwd_uniform_noalloc(const adj_1d_desc_t* tf_h, const adj_1d_desc_t* tf_v, int64_t n_blocks,
                                       const int16_t* d_resid, float* d_coef, void* stream);
+
+/*
+ * CUDA graphs of a plan's launches for fixed buffers (captured once, replayed by
+ * adj_graph_launch).  `what` selects the launches:
+ *   ADJ_GRAPH_FWD / ADJ_GRAPH_INV              the fused kernel (d_in -> d_out)
+ *   ADJ_GRAPH_FWD_PLAIN / ADJ_GRAPH_INV_PLAIN  the plain form (d_in -> d_out)
+ *   ADJ_GRAPH_ROUNDTRIP                        fused forward d_in -> d_out, then fused
+ *                                              inverse d_out -> d_out2
+ * The graph refers to the plan's tables: replace neither the block list nor the plan while
+ * it exists (adj_plan_update_params is fine).  Errors: INVALID_ARG, NO_BLOCKS, MISALIGNED, CUDA.
+ */
+typedef struct adj_graph adj_graph_t;
+enum { ADJ_GRAPH_FWD = 0, ADJ_GRAPH_INV = 1, ADJ_GRAPH_FWD_PLAIN = 2, ADJ_GRAPH_INV_PLAIN = 3,
+       ADJ_GRAPH_ROUNDTRIP = 4 };
+int adj_graph_create(adj_plan_t* plan, int32_t what, const void* d_in, float* d_out, float* d_out2,
+                     adj_graph_t** graph);
+int adj_graph_launch(adj_graph_t* graph, void* stream);
+void adj_graph_destroy(adj_graph_t* graph);
 
 /* Launch geometry and tile statistics of a plan (for benchmarks and tests). */
 typedef struct {

@@ -42,7 +42,7 @@ import numpy as np
 
 __all__ = [
     "CORE_DCT2", "CORE_DCT3", "CORE_DST2", "CORE_DST3",
-    "KIND_NONE", "KIND_BAND", "KIND_POST",
+    "KIND_NONE", "KIND_BAND", "KIND_POST", "KIND_DENSE",
     "dct2", "dct3", "dst2", "dst3", "dst7", "dct8", "dct4",
     "reversal", "alt_sign", "core_matrix",
     "layer_pairs", "givens_layer", "band_matrix", "post_matrix",
@@ -53,7 +53,7 @@ __all__ = [
 ]
 
 CORE_DCT2, CORE_DCT3, CORE_DST2, CORE_DST3 = 0, 1, 2, 3
-KIND_NONE, KIND_BAND, KIND_POST = 0, 1, 2
+KIND_NONE, KIND_BAND, KIND_POST, KIND_DENSE = 0, 1, 2, 3
 
 
 # --------------------------------------------------------------------------
@@ -199,6 +199,12 @@ def adjusted_matrix(N, core, kind, parities=(), angles=(), Q=None) -> np.ndarray
         return B @ band_matrix(N, parities, angles)
     if kind == KIND_POST:
         return post_matrix(N, Q) @ B
+    if kind == KIND_DENSE:
+        # the reference the adjustments approximate: a given dense orthogonal matrix D
+        Q = np.asarray(Q, dtype=np.float64)
+        if Q.shape != (N, N):
+            raise ValueError("a dense transform is N x N")
+        return Q.copy()
     raise ValueError(f"unknown adjustment kind {kind}")
 
 
@@ -210,7 +216,7 @@ def tf_matrix(tf) -> np.ndarray:
         int(get("n")), int(get("core")), kind,
         parities=get("parities") if kind == KIND_BAND else (),
         angles=get("angles") if kind == KIND_BAND else (),
-        Q=get("q") if kind == KIND_POST else None,
+        Q=get("q") if kind in (KIND_POST, KIND_DENSE) else None,
     )
 
 

@@ -29,8 +29,12 @@ EXPORTED = (
     "adj_plan_create", "adj_plan_set_blocks", "adj_plan_update_params",
     "adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host",
     "adj_transform_inv_host", "adj_plan_info", "adj_plan_destroy", "adj_last_error",
-    "adj_transform_fwd_uniform_noalloc",
+    "adj_transform_fwd_uniform_noalloc", "adj_transform_fwd_plain", "adj_transform_inv_plain",
+    "adj_graph_create", "adj_graph_launch", "adj_graph_destroy", "adj_transform_bwd",
+    "adj_plan_param_layout",
 )
+DTYPE_INT16, DTYPE_FP32 = 0, 1
+GRAPH_FWD, GRAPH_INV, GRAPH_FWD_PLAIN, GRAPH_INV_PLAIN, GRAPH_ROUNDTRIP = range(5)
 
 
 class Adj1dDesc(C.Structure):
@@ -65,15 +69,22 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.adj_plan_create.argtypes = [C.POINTER(vp), C.POINTER(Adj1dDesc), i32, i32]
     lib.adj_plan_set_blocks.argtypes = [vp, vp, i64, i64]
     lib.adj_plan_update_params.argtypes = [vp, C.POINTER(Adj1dDesc), i32]
-    for f in ("adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host", "adj_transform_inv_host"):
+    for f in ("adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host", "adj_transform_inv_host",
+              "adj_transform_fwd_plain", "adj_transform_inv_plain"):
         getattr(lib, f).argtypes = [vp, vp, vp, vp]
     lib.adj_plan_info.argtypes = [vp, C.POINTER(AdjPlanInfo)]
     lib.adj_transform_fwd_uniform_noalloc.argtypes = [C.POINTER(Adj1dDesc), C.POINTER(Adj1dDesc), i64, vp, vp, vp]
+    lib.adj_transform_bwd.argtypes = [vp, vp, i32, vp, vp, vp, vp]
+    lib.adj_plan_param_layout.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.adj_graph_create.argtypes = [vp, i32, vp, vp, vp, C.POINTER(vp)]
+    lib.adj_graph_launch.argtypes = [vp, vp]
+    lib.adj_graph_destroy.argtypes = [vp]
+    lib.adj_graph_destroy.restype = None
     lib.adj_plan_destroy.argtypes = [vp]
     lib.adj_plan_destroy.restype = None
     lib.adj_last_error.restype = C.c_char_p
     for f in EXPORTED:
-        if f not in ("adj_plan_destroy", "adj_last_error"):
+        if f not in ("adj_plan_destroy", "adj_last_error", "adj_graph_destroy"):
             getattr(lib, f).restype = C.c_int
     return lib
 
@@ -116,7 +127,7 @@ class _DescArray:
                 d.layer_parity = par.ctypes.data_as(C.POINTER(C.c_uint8))
                 d.angles = ang.ctypes.data_as(C.POINTER(C.c_double))
                 self.keep += [par, ang]
-            if d.kind == 2 and q is not None:
+            if d.kind in (2, 3) and q is not None:
                 qa = np.ascontiguousarray(q, dtype=np.float64)
                 d.k = qa.shape[0]
                 d.q = qa.ctypes.data_as(C.POINTER(C.c_double))
@@ -174,11 +185,34 @@ class Plan:
     def inv(self, d_in, d_out, stream=None):
         check(self._lib.adj_transform_inv(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
 
+    def fwd_plain(self, d_in, d_out, stream=None):
+        check(self._lib.adj_transform_fwd_plain(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+    def inv_plain(self, d_in, d_out, stream=None):
+        check(self._lib.adj_transform_inv_plain(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
     def fwd_host(self, h_in, h_out, stream=None):
         check(self._lib.adj_transform_fwd_host(self._h, _ptr(h_in), _ptr(h_out), _stream(stream)))
 
     def inv_host(self, h_in, h_out, stream=None):
         check(self._lib.adj_transform_inv_host(self._h, _ptr(h_in), _ptr(h_out), _stream(stream)))
+
+    def bwd(self, d_x, d_gy, d_gx=None, d_gparams=None, stream=None, x_fp32=None):
+        """Gradients of the forward transform (see adj_transform_bwd)."""
+        if x_fp32 is None:
+            x_fp32 = getattr(d_x, "dtype", None) is not None and "float" in str(d_x.dtype)
+        check(self._lib.adj_transform_bwd(self._h, _ptr(d_x), DTYPE_FP32 if x_fp32 else DTYPE_INT16,
+                                          _ptr(d_gy), _ptr(d_gx), _ptr(d_gparams), _stream(stream)))
+
+    def param_layout(self):
+        """Offsets of each transform's gradient entries (n_tfs + 1 values)."""
+        off = (C.c_int32 * (len(self.tfs) + 1))()
+        check(self._lib.adj_plan_param_layout(self._h, off))
+        return list(off)
+
+    def graph(self, what, d_in, d_out, d_out2=None):
+        """Capture the selected launches for these buffers; returns a Graph."""
+        return Graph(self, what, d_in, d_out, d_out2)
 
     def info(self) -> dict:
         i = AdjPlanInfo()
@@ -201,3 +235,28 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Graph:
+    """An adj_graph_t: captured launches of a plan for fixed buffers."""
+
+    def __init__(self, plan, what, d_in, d_out, d_out2=None):
+        self._lib = plan._lib
+        self.plan = plan            # keeps the plan alive while the graph exists
+        self._h = C.c_void_p()
+        check(self._lib.adj_graph_create(plan._h, int(what), _ptr(d_in), _ptr(d_out), _ptr(d_out2),
+                                         C.byref(self._h)))
+
+    def launch(self, stream=None):
+        check(self._lib.adj_graph_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            self._lib.adj_graph_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -74,6 +74,15 @@ struct adj_plan {
   void* d_host_in = nullptr;
   float* d_host_out = nullptr;
   size_t host_cap = 0;
+  PlainBlock* d_plain = nullptr;       // plain form: blocks grouped by size
+  std::vector<PlainClass> plain;
+  // backward: accumulator and gradient layouts per transform, scratch
+  std::vector<int> m_off, g_off, kq;
+  int P = 0, n_grad = 0;
+  int* d_layout = nullptr;             // m_off | g_off | kq on the device
+  float* d_partial = nullptr;
+  double* d_M = nullptr;
+  int bwd_grid = 0;
 };
 
 namespace {
@@ -81,7 +90,9 @@ namespace {
 int validate_tf(const adj_1d_desc_t& d, int idx, TfHost* out) {
   if (!is_size(d.n)) return fail(ADJ_ERR_UNSUPPORTED_SIZE, "tf %d: n=%d not in {4,8,16,32,64}", idx, d.n);
   if (d.core < 0 || d.core > 3) return fail(ADJ_ERR_INVALID_ARG, "tf %d: core %d", idx, d.core);
-  if (d.kind < 0 || d.kind > 2) return fail(ADJ_ERR_INVALID_ARG, "tf %d: kind %d", idx, d.kind);
+  if (d.kind < 0 || d.kind > 3) return fail(ADJ_ERR_INVALID_ARG, "tf %d: kind %d", idx, d.kind);
+  if (d.kind == ADJ_ADJ_DENSE && d.k != d.n)
+    return fail(ADJ_ERR_PARAM_MISMATCH, "tf %d: a dense transform needs k = n (%d, %d)", idx, d.k, d.n);
   TfHost t{};
   t.n = d.n;
   t.core = d.core;
@@ -102,7 +113,7 @@ int validate_tf(const adj_1d_desc_t& d, int idx, TfHost* out) {
     t.angles.assign(d.angles, d.angles + np);
     for (double a : t.angles)
       if (!std::isfinite(a)) return fail(ADJ_ERR_PARAM_MISMATCH, "tf %d: non-finite angle", idx);
-  } else if (d.kind == ADJ_ADJ_POST_BLOCK) {
+  } else if (d.kind == ADJ_ADJ_POST_BLOCK || d.kind == ADJ_ADJ_DENSE) {
     if (d.k < 1 || d.k > d.n) return fail(ADJ_ERR_UNSUPPORTED_SIZE, "tf %d: K=%d with n=%d", idx, d.k, d.n);
     if (!d.q) return fail(ADJ_ERR_INVALID_ARG, "tf %d: null q", idx);
     t.k = d.k;
@@ -148,7 +159,7 @@ void materialise(const std::vector<TfHost>& tfs, std::vector<float>* params, std
         params->push_back((float)std::cos(a));
         params->push_back((float)std::sin(a));
       }
-    } else if (t.kind == ADJ_ADJ_POST_BLOCK) {
+    } else if (t.kind == ADJ_ADJ_POST_BLOCK || t.kind == ADJ_ADJ_DENSE) {
       d.kt = t.kt;
       while (params->size() % 4) params->push_back(0.f);
       d.q_off = (uint32_t)params->size();
@@ -185,6 +196,9 @@ void free_blocks(adj_plan* p) {
   cudaFree(p->d_tiles);
   cudaFree(p->d_tile_blk);
   cudaFree(p->d_range_begin);
+  cudaFree(p->d_plain);
+  p->d_plain = nullptr;
+  p->plain.clear();
   p->d_tiles = nullptr;
   p->d_tile_blk = nullptr;
   p->d_range_begin = nullptr;
@@ -218,6 +232,60 @@ int run(adj_plan* p, bool inverse, const void* in, float* out, cudaStream_t stre
   a.n_ranges = p->n_ranges;
   cudaError_t e = launch_fused(inverse, p->threads, inverse ? p->grid_inv : p->grid_fwd, a, stream);
   if (e != cudaSuccess) return cuda_fail(e, inverse ? "inverse launch" : "forward launch");
+  return ADJ_OK;
+}
+
+int run_bwd(adj_plan* p, const void* x, bool x_f32, const float* gy, float* gx, float* gparams, cudaStream_t stream) {
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  int rc;
+  if ((rc = check_ptr(x, "input")) || (rc = check_ptr(gy, "output gradient"))) return rc;
+  if (gx && (rc = check_ptr(gx, "input gradient"))) return rc;
+  if (gparams && (rc = check_ptr(gparams, "parameter gradient"))) return rc;
+  if (p->n_tiles == 0) {
+    if (gparams && p->n_grad) CUDA_TRY(cudaMemsetAsync(gparams, 0, p->n_grad * sizeof(float), stream));
+    return ADJ_OK;
+  }
+  if (!p->bwd_grid) {
+    const void* fn = bwd_kernel_ptr(true);
+    const void* fn2 = bwd_kernel_ptr(false);
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem_bytes()));
+    CUDA_TRY(cudaFuncSetAttribute(fn2, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem_bytes()));
+    int occ = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBwdThreads, bwd_smem_bytes()));
+    p->bwd_grid = std::max(1, occ) * p->n_sm;
+  }
+  const int grid = std::min(p->bwd_grid, p->n_tiles);
+  if (!p->d_partial && p->P) {
+    CUDA_TRY(cudaMalloc(&p->d_partial, (size_t)p->bwd_grid * p->P * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&p->d_M, (size_t)p->P * sizeof(double)));
+  }
+  BwdArgs a{};
+  a.tiles = p->d_tiles;
+  a.tile_blk = p->d_tile_blk;
+  a.tfs = p->d_tfs;
+  a.params = p->d_params;
+  a.x = x;
+  a.gy = gy;
+  a.gx = gx;
+  a.partial = p->d_partial;
+  a.m_off = p->d_layout;
+  a.n_tiles = p->n_tiles;
+  a.P = p->P;
+  const int n = (int)p->tfs.size();
+  cudaError_t e = launch_bwd(!x_f32, grid, a, p->d_M, p->d_tfs, n, p->d_layout, p->d_layout + n, p->d_layout + 2 * n,
+                             gparams, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return ADJ_OK;
+}
+
+int run_plain(adj_plan* p, bool inverse, const void* in, float* out, cudaStream_t stream) {
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  int rc;
+  if ((rc = check_ptr(in, "input")) || (rc = check_ptr(out, "output"))) return rc;
+  cudaError_t e = launch_plain(inverse, p->plain.data(), (int)p->plain.size(), p->d_tfs, p->d_params, in, out, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "plain-form launch");
   return ADJ_OK;
 }
 
@@ -258,6 +326,71 @@ extern "C" {
 
 const char* adj_last_error(void) { return g_err.c_str(); }
 
+struct adj_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+int adj_graph_create(adj_plan_t* p, int32_t what, const void* d_in, float* d_out, float* d_out2, adj_graph_t** graph) {
+  g_err.clear();
+  if (!graph) return fail(ADJ_ERR_INVALID_ARG, "null graph pointer");
+  *graph = nullptr;
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (what < ADJ_GRAPH_FWD || what > ADJ_GRAPH_ROUNDTRIP) return fail(ADJ_ERR_INVALID_ARG, "unknown graph kind %d", what);
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  int rc;
+  if ((rc = check_ptr(d_in, "input")) || (rc = check_ptr(d_out, "output"))) return rc;
+  if (what == ADJ_GRAPH_ROUNDTRIP && (rc = check_ptr(d_out2, "second output"))) return rc;
+  cudaStream_t s = nullptr;
+  CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  switch (what) {
+    case ADJ_GRAPH_FWD: rc = run(p, false, d_in, d_out, s); break;
+    case ADJ_GRAPH_INV: rc = run(p, true, d_in, d_out, s); break;
+    case ADJ_GRAPH_FWD_PLAIN: rc = run_plain(p, false, d_in, d_out, s); break;
+    case ADJ_GRAPH_INV_PLAIN: rc = run_plain(p, true, d_in, d_out, s); break;
+    default:
+      rc = run(p, false, d_in, d_out, s);
+      if (!rc) rc = run(p, true, d_out, d_out2, s);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  cudaStreamDestroy(s);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  adj_graph* out = new adj_graph();
+  out->graph = g;
+  e = cudaGraphInstantiate(&out->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    delete out;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  *graph = out;
+  return ADJ_OK;
+}
+
+int adj_graph_launch(adj_graph_t* g, void* stream) {
+  g_err.clear();
+  if (!g) return fail(ADJ_ERR_INVALID_ARG, "null graph");
+  CUDA_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+  return ADJ_OK;
+}
+
+void adj_graph_destroy(adj_graph_t* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
 }  // extern "C"
 
 // Lets other translation units of the library report errors through adj_last_error().
@@ -285,6 +418,26 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     return cuda_fail(e, "device query");
   }
   int rc = upload_params(p);
+  // gradient layouts: accumulator side^2 per transform (band n, post / dense kt) and the
+  // gradient entries (band: angles, post: K x K, dense: n x n)
+  for (const TfHost& t : p->tfs) {
+    const int side = t.kind == ADJ_ADJ_PRE_BAND ? t.n : (t.kind >= ADJ_ADJ_POST_BLOCK ? t.kt : 0);
+    const int ng = t.kind == ADJ_ADJ_PRE_BAND ? t.n_pairs : (t.kind >= ADJ_ADJ_POST_BLOCK ? t.k * t.k : 0);
+    p->m_off.push_back(p->P);
+    p->g_off.push_back(p->n_grad);
+    p->kq.push_back(t.k);
+    p->P += side * side;
+    p->n_grad += ng;
+  }
+  p->g_off.push_back(p->n_grad);
+  if (!rc && !p->tfs.empty()) {
+    std::vector<int> lay(p->m_off);
+    lay.insert(lay.end(), p->g_off.begin(), p->g_off.end() - 1);
+    lay.insert(lay.end(), p->kq.begin(), p->kq.end());
+    e = cudaMalloc(&p->d_layout, lay.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_layout, lay.data(), lay.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_fail(e, "gradient layout upload");
+  }
   if (!rc) {
     e = cudaMalloc(&p->d_sched, 2 * sizeof(SchedState));
     if (e == cudaSuccess) e = cudaMemset(p->d_sched, 0, 2 * sizeof(SchedState));
@@ -428,7 +581,29 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
     rbeg.push_back((unsigned)tiles.size());
   }
 
+  // Plain form: blocks grouped by size, in storage order within a size.
+  std::vector<PlainBlock> pblk;
+  std::vector<PlainClass> pcls;
+  for (int lw = 2; lw <= 6; ++lw)
+    for (int lh = 2; lh <= 6; ++lh) {
+      PlainClass c{1 << lw, 1 << lh, 0, nullptr};
+      const size_t first = pblk.size();
+      for (int64_t i : order) {
+        const adj_block_t& b = blocks[i];
+        if (b.w == c.w && b.h == c.h) pblk.push_back(PlainBlock{(uint32_t)(b.offset / 16), b.tf_h, b.tf_v});
+      }
+      c.n_blocks = (int)(pblk.size() - first);
+      c.blocks = reinterpret_cast<const PlainBlock*>(first);  // index for now, pointer after upload
+      if (c.n_blocks) pcls.push_back(c);
+    }
+
   free_blocks(p);
+  if (!pblk.empty()) {
+    CUDA_TRY(cudaMalloc(&p->d_plain, pblk.size() * sizeof(PlainBlock)));
+    CUDA_TRY(cudaMemcpy(p->d_plain, pblk.data(), pblk.size() * sizeof(PlainBlock), cudaMemcpyHostToDevice));
+    for (PlainClass& c : pcls) c.blocks = p->d_plain + reinterpret_cast<size_t>(c.blocks);
+  }
+  p->plain = pcls;
   if (!tiles.empty()) {
     CUDA_TRY(cudaMalloc(&p->d_tiles, tiles.size() * sizeof(TileDev)));
     CUDA_TRY(cudaMalloc(&p->d_tile_blk, tblk.size() * sizeof(uint32_t)));
@@ -453,6 +628,30 @@ int adj_transform_fwd(adj_plan_t* p, const int16_t* d_resid, float* d_coef, void
 int adj_transform_inv(adj_plan_t* p, const float* d_coef, float* d_resid_out, void* stream) {
   g_err.clear();
   return run(p, true, d_coef, d_resid_out, static_cast<cudaStream_t>(stream));
+}
+
+int adj_transform_bwd(adj_plan_t* p, const void* d_x, int32_t x_dtype, const float* d_gy, float* d_gx,
+                      float* d_gparams, void* stream) {
+  g_err.clear();
+  if (x_dtype != ADJ_DTYPE_INT16 && x_dtype != ADJ_DTYPE_FP32) return fail(ADJ_ERR_INVALID_ARG, "x_dtype %d", x_dtype);
+  return run_bwd(p, d_x, x_dtype == ADJ_DTYPE_FP32, d_gy, d_gx, d_gparams, static_cast<cudaStream_t>(stream));
+}
+
+int adj_plan_param_layout(const adj_plan_t* p, int32_t* offsets) {
+  g_err.clear();
+  if (!p || !offsets) return fail(ADJ_ERR_INVALID_ARG, "null argument");
+  for (size_t i = 0; i < p->g_off.size(); ++i) offsets[i] = p->g_off[i];
+  return ADJ_OK;
+}
+
+int adj_transform_fwd_plain(adj_plan_t* p, const int16_t* d_resid, float* d_coef, void* stream) {
+  g_err.clear();
+  return run_plain(p, false, d_resid, d_coef, static_cast<cudaStream_t>(stream));
+}
+
+int adj_transform_inv_plain(adj_plan_t* p, const float* d_coef, float* d_resid_out, void* stream) {
+  g_err.clear();
+  return run_plain(p, true, d_coef, d_resid_out, static_cast<cudaStream_t>(stream));
 }
 
 int adj_transform_fwd_host(adj_plan_t* p, const int16_t* h_resid, float* h_coef, void* stream) {
@@ -487,6 +686,9 @@ void adj_plan_destroy(adj_plan_t* p) {
   cudaFree(p->d_sched);
   cudaFree(p->d_host_in);
   cudaFree(p->d_host_out);
+  cudaFree(p->d_layout);
+  cudaFree(p->d_partial);
+  cudaFree(p->d_M);
   delete p;
 }
 

@@ -268,15 +268,15 @@ __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __r
   }
   if (!INV) {
     if (tf.kind == KIND_BAND) band<N, false>(v, tf, P);
-    core_apply<N>(tf.core, v);
-    if (tf.kind == KIND_POST) {
+    if (tf.kind != KIND_DENSE) core_apply<N>(tf.core, v);
+    if (tf.kind >= KIND_POST) {
       post_fwd<N>(v, tf, P, dst);
     } else {
       dst.template store<N>(v);
     }
   } else {
-    if (tf.kind == KIND_POST) post_inv<N>(v, tf, P, src);
-    core_apply<N>(tf.core ^ 1, v);
+    if (tf.kind >= KIND_POST) post_inv<N>(v, tf, P, src);
+    if (tf.kind != KIND_DENSE) core_apply<N>(tf.core ^ 1, v);
     if (tf.kind == KIND_BAND) band<N, true>(v, tf, P);
     dst.template store<N>(v);
   }
@@ -306,7 +306,7 @@ __device__ __forceinline__ unsigned sm_id() {
 // Completes a claim whose atomicAdd on s->pos[range] returned k (issued earlier, so its
 // latency overlapped other work): the tile index, or the result of a full search when
 // the range turned out to be exhausted.
-__device__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges, int& range);
+static __device__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges, int& range);
 __device__ __forceinline__ int claim_resolve(SchedState* s, const unsigned* __restrict__ begin, int n_ranges,
                                              int& range, unsigned k) {
   const unsigned t = __ldg(begin + range) + k;
@@ -327,7 +327,7 @@ __device__ __forceinline__ int next_open_range(const unsigned* ex, int from, int
 // `range` is the CTA's current range (initially -1: start at the SM's own range).
 // Every probe either returns a tile or marks one more range exhausted, so the loop ends
 // after at most 2 * n_ranges + 2 probes.
-__device__ __noinline__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges,
+static __device__ __noinline__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges,
                                        int& range) {
   if (range < 0) range = (int)(sm_id() % (unsigned)n_ranges);
   unsigned ex[kMaxRanges / 32];

@@ -21,6 +21,38 @@ struct FusedArgs {
   int n_ranges;
 };
 
+// Plain (unfused) form: the blocks of one size class, each with its own transforms.
+struct PlainBlock {
+  uint32_t off16;
+  uint16_t tf_h, tf_v;
+};
+struct PlainClass {
+  int w, h, n_blocks;
+  const PlainBlock* blocks;  // device
+};
+cudaError_t launch_plain(bool inverse, const PlainClass* classes, int n_classes, const TfDev* tfs, const float* P,
+                         const void* in, float* out, cudaStream_t stream);
+
+// Backward (parameter and input gradients).
+constexpr int kBwdThreads = 128;
+struct BwdArgs {
+  const TileDev* tiles;
+  const uint32_t* tile_blk;
+  const TfDev* tfs;
+  const float* params;
+  const void* x;        // int16 or FP32 input of the forward
+  const float* gy;      // dL/dY
+  float* gx;            // dL/dX (may be null)
+  float* partial;       // [grid][P] per-CTA sums
+  const int* m_off;     // per transform: offset of its accumulator in a row of `partial`
+  int n_tiles;
+  int P;
+};
+int bwd_smem_bytes();
+const void* bwd_kernel_ptr(bool i16);
+cudaError_t launch_bwd(bool i16, int grid, const BwdArgs& args, double* M, const TfDev* tfs, int n_tfs,
+                       const int* m_off, const int* g_off, const int* kq, float* gparams, cudaStream_t stream);
+
 const void* fused_kernel_ptr(bool inverse, int threads);
 void set_last_error(const char* msg);
 cudaError_t launch_fused(bool inverse, int threads, int grid, const FusedArgs& args, cudaStream_t stream);

@@ -12,7 +12,7 @@
 
 namespace adjtx {
 
-enum { KIND_NONE = 0, KIND_BAND = 1, KIND_POST = 2 };
+enum { KIND_NONE = 0, KIND_BAND = 1, KIND_POST = 2, KIND_DENSE = 3 };
 
 // One 1-D transform as the kernels see it (parameters live in one FP32 buffer).
 struct TfDev {

@@ -98,7 +98,9 @@ int pack_tf(const adj_1d_desc_t* d, const char* name, TfDev* rec, float* params,
   if (!d) return err(ADJ_ERR_INVALID_ARG, "%s is null", name);
   if (!is_size(d->n)) return err(ADJ_ERR_UNSUPPORTED_SIZE, "%s: n=%d not in {4,8,16,32,64}", name, d->n);
   if (d->core < 0 || d->core > 3) return err(ADJ_ERR_INVALID_ARG, "%s: core %d", name, d->core);
-  if (d->kind < 0 || d->kind > 2) return err(ADJ_ERR_INVALID_ARG, "%s: kind %d", name, d->kind);
+  if (d->kind < 0 || d->kind > 3) return err(ADJ_ERR_INVALID_ARG, "%s: kind %d", name, d->kind);
+  if (d->kind == ADJ_ADJ_DENSE && d->k != d->n)
+    return err(ADJ_ERR_PARAM_MISMATCH, "%s: a dense transform needs k = n", name);
   std::memset(rec, 0, sizeof *rec);
   rec->n = d->n;
   rec->core = d->core;
@@ -128,7 +130,7 @@ int pack_tf(const adj_1d_desc_t* d, const char* name, TfDev* rec, float* params,
       params[np++] = (float)std::cos(d->angles[i]);
       params[np++] = (float)std::sin(d->angles[i]);
     }
-  } else if (d->kind == ADJ_ADJ_POST_BLOCK) {
+  } else if (d->kind == ADJ_ADJ_POST_BLOCK || d->kind == ADJ_ADJ_DENSE) {
     const int k = d->k;
     if (k < 1 || k > d->n) return err(ADJ_ERR_UNSUPPORTED_SIZE, "%s: K=%d with n=%d", name, k, d->n);
     if (!d->q) return err(ADJ_ERR_INVALID_ARG, "%s: null q", name);

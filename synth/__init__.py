@@ -20,7 +20,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 CORE_DCT2, CORE_DCT3, CORE_DST2, CORE_DST3 = 0, 1, 2, 3
-KIND_NONE, KIND_BAND, KIND_POST = 0, 1, 2
+KIND_NONE, KIND_BAND, KIND_POST, KIND_DENSE = 0, 1, 2, 3
 SIZES = (4, 8, 16, 32, 64)
 
 BLOCK_DTYPE = np.dtype([("offset", "<i8"), ("w", "<u2"), ("h", "<u2"),

@@ -82,7 +82,9 @@ def _q(k, seed=0):
     (dict(n=12, core=0, kind=0), "ADJ_ERR_UNSUPPORTED_SIZE"),
     (dict(n=2, core=0, kind=0), "ADJ_ERR_UNSUPPORTED_SIZE"),
     (dict(n=8, core=4, kind=0), "ADJ_ERR_INVALID_ARG"),
-    (dict(n=8, core=0, kind=3), "ADJ_ERR_INVALID_ARG"),
+    (dict(n=8, core=0, kind=4), "ADJ_ERR_INVALID_ARG"),
+    (dict(n=8, core=0, kind=3, q=_q(4)), "ADJ_ERR_PARAM_MISMATCH"),
+    (dict(n=8, core=0, kind=3, q=3 * _q(8)), "ADJ_ERR_PARAM_MISMATCH"),
     (dict(n=8, core=0, kind=2, q=_q(9)), "ADJ_ERR_UNSUPPORTED_SIZE"),
     (dict(n=8, core=0, kind=2, q=2 * _q(4)), "ADJ_ERR_PARAM_MISMATCH"),
     (dict(n=8, core=0, kind=1, parities=np.array([0, 2], np.uint8), angles=np.zeros(7)), "ADJ_ERR_INVALID_ARG"),
