@@ -156,6 +156,17 @@ int adj_transform_bwd(adj_plan_t* plan, const void* d_x, int32_t x_dtype, const 
 int adj_plan_param_layout(const adj_plan_t* plan, int32_t* offsets);
 
 /*
+ * Coding-gain proxy of coefficient blocks, the objective beside Eq. 2 that the fitter
+ * minimises: for n_blocks blocks of hw coefficients stored back to back in d_y (FP32,
+ * device), var[p] = mean_b Y_b[p]^2, *d_loss = (1/hw) sum_p log var[p] (FP64, device), and,
+ * if d_gy is given, dL/dY = 2 Y / (hw n var) (FP32, device, same layout as d_y).  d_work is
+ * caller-owned device scratch of 65 * hw doubles.  Sums are in a fixed order.
+ * Errors: INVALID_ARG (hw not in 1..4096), CUDA.
+ */
+int adj_coding_gain_proxy(const float* d_y, int64_t n_blocks, int32_t hw, double* d_work, double* d_loss, float* d_gy,
+                          void* stream);
+
+/*
  * Plain (unfused) form of the same transforms, the baseline the fused path is measured
  * against: for every block size present, one launch per step of the chain (band, core,
  * post) along the rows, then along the columns (forward; the inverse runs the transposed

@@ -31,7 +31,7 @@ EXPORTED = (
     "adj_transform_inv_host", "adj_plan_info", "adj_plan_destroy", "adj_last_error",
     "adj_transform_fwd_uniform_noalloc", "adj_transform_fwd_plain", "adj_transform_inv_plain",
     "adj_graph_create", "adj_graph_launch", "adj_graph_destroy", "adj_transform_bwd",
-    "adj_plan_param_layout",
+    "adj_plan_param_layout", "adj_coding_gain_proxy",
 )
 DTYPE_INT16, DTYPE_FP32 = 0, 1
 GRAPH_FWD, GRAPH_INV, GRAPH_FWD_PLAIN, GRAPH_INV_PLAIN, GRAPH_ROUNDTRIP = range(5)
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.adj_transform_fwd_uniform_noalloc.argtypes = [C.POINTER(Adj1dDesc), C.POINTER(Adj1dDesc), i64, vp, vp, vp]
     lib.adj_transform_bwd.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.adj_plan_param_layout.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.adj_coding_gain_proxy.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     lib.adj_graph_create.argtypes = [vp, i32, vp, vp, vp, C.POINTER(vp)]
     lib.adj_graph_launch.argtypes = [vp, vp]
     lib.adj_graph_destroy.argtypes = [vp]

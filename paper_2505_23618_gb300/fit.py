@@ -1,0 +1,304 @@
+"""Gradient fit of the adjustment parameters (the design step of Eq. 2, driven by the GPU
+backward kernel).
+
+Loss (per fitted 1-D transform H of length N, used both horizontally and vertically):
+    L = sum_{k<M} |h_k - d_k|^2  +  lam * P(H),
+where h_k, d_k are the first M basis vectors (rows) of H and of the target D (DST-7), and
+P is the coding-gain proxy of the 2-D coefficients of synthetic AR(1) blocks,
+(1/N^2) sum_{kv,kh} log mean_b Y_b[kv,kh]^2.  Optionally the paper's weighted criterion of
+Eq. 2 replaces the first term: sum_{i,j} e^{-alpha i} (H_ij - D_ij)^2, alpha = ln(100)/N.
+
+Parameterisations (orthogonality by construction, Section 2 after Eq. 2):
+    band  H = B A(theta), A a product of Givens layers; theta are the free parameters;
+    post  H = diag(Q, I) B with Q = Dg (I + W)^{-1} (I - W), W skew-symmetric (the Cayley
+          map; Dg a fixed +-1 diagonal taken from the start point, since the Cayley map only
+          reaches det = +1 without an eigenvalue -1).
+
+The GPU does the per-block work (forward of every block, the proxy and its gradient, the
+backward into dL/dtheta or dL/dQ); the host keeps the N x N FP64 model of H for the basis
+term, the Cayley map and Adam.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import json
+import math
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _lib, targets
+
+
+# ---------------------------------------------------------------------------------------
+# FP64 host model of one direction's H and of its parameter gradients.
+# ---------------------------------------------------------------------------------------
+
+def _layer_pairs(n, parity):
+    return [(i, i + 1) for i in range(int(parity), n - 1, 2)]
+
+
+def _rot_layer(n, parity, angles):
+    G = np.eye(n)
+    for (i, j), th in zip(_layer_pairs(n, parity), angles):
+        c, s = math.cos(th), math.sin(th)
+        G[i, i], G[i, j], G[j, i], G[j, j] = c, -s, s, c
+    return G
+
+
+def band_layers(n, parities, angles):
+    out, pos = [], 0
+    for p in parities:
+        cnt = len(_layer_pairs(n, p))
+        out.append(_rot_layer(n, p, angles[pos:pos + cnt]))
+        pos += cnt
+    return out
+
+
+def band_H(n, core, parities, angles):
+    A = np.eye(n)
+    for G in band_layers(n, parities, angles):
+        A = G @ A
+    return targets.core(n, core) @ A
+
+
+def band_angle_grad(n, core, parities, angles, dH):
+    """dL/dtheta for H = B G_{L-1}...G_0 from dL/dH (FP64, by the product rule per layer)."""
+    Gs = band_layers(n, parities, angles)
+    dA = targets.core(n, core).T @ dH
+    out = np.zeros(len(angles))
+    pos = 0
+    for l, p in enumerate(parities):
+        left = np.eye(n)
+        for m in range(len(Gs) - 1, l, -1):
+            left = left @ Gs[m]
+        right = np.eye(n)
+        for m in range(l):
+            right = Gs[m] @ right
+        M = left.T @ dA @ right.T
+        for q, (i, j) in enumerate(_layer_pairs(n, p)):
+            c, s = math.cos(angles[pos + q]), math.sin(angles[pos + q])
+            out[pos + q] = -s * M[i, i] - c * M[i, j] + c * M[j, i] - s * M[j, j]
+        pos += len(_layer_pairs(n, p))
+    return out
+
+
+def skew(w, k):
+    W = np.zeros((k, k))
+    W[np.triu_indices(k, 1)] = w
+    return W - W.T
+
+
+def cayley_q(w, k, dg):
+    W = skew(w, k)
+    I = np.eye(k)
+    return dg[:, None] * np.linalg.solve(I + W, I - W)
+
+
+def cayley_grad(w, k, dg, gq):
+    W = skew(w, k)
+    I = np.eye(k)
+    Cq = np.linalg.solve(I + W, I - W)
+    M = -np.linalg.solve((I + W).T, dg[:, None] * gq) @ (Cq + I).T
+    return (M - M.T)[np.triu_indices(k, 1)]
+
+
+def cayley_init(q):
+    """(w, dg) with Dg Cayley(W) = q for an orthogonal q whose Dg q has no eigenvalue -1."""
+    k = q.shape[0]
+    # choose the signs so that Dg q is as close to I as the diagonal allows
+    dg = np.where(np.diag(q) < 0, -1.0, 1.0)
+    C0 = dg[:, None] * q
+    I = np.eye(k)
+    W = np.linalg.solve(I + C0, I - C0)   # inverse Cayley map
+    W = 0.5 * (W - W.T)
+    return W[np.triu_indices(k, 1)], dg
+
+
+# ---------------------------------------------------------------------------------------
+# The fit.
+# ---------------------------------------------------------------------------------------
+
+@dataclass
+class FitConfig:
+    n: int = 64
+    core: int = 0                 # 0 DCT-2, 1 DCT-3, 2 DST-2, 3 DST-3
+    kind: int = 1                 # 1 band, 2 post
+    parities: tuple = (0, 1) * 6  # band layers
+    k: int = 32                   # post block size
+    target: str = "dst7"
+    m: int = 16                   # basis vectors matched
+    lam: float = 0.1              # weight of the coding-gain proxy
+    eq2: bool = False             # use the paper's weighted criterion (Eq. 2) instead
+    blocks: int = 65536
+    rho: float = 0.95
+    sigma: float = 40.0
+    seed: int = 4
+    steps: int = 200
+    lr: float = 0.01
+    history: list = field(default_factory=list)
+
+
+class Fitter:
+    """Fits one 1-D adjusted transform on the GPU (one plan, blocks of n x n)."""
+
+    def __init__(self, cfg: FitConfig, data=None, device=None):
+        import torch
+
+        self.cfg = cfg
+        self.torch = torch
+        self.dev = torch.device(device or "cuda")
+        n = cfg.n
+        self.D = {"dst7": targets.dst7, "dct8": targets.dct8}[cfg.target](n)
+        if data is None:
+            import synth
+            rng = np.random.default_rng(cfg.seed)
+            data = synth.ar1_blocks(rng, cfg.blocks, n, n, cfg.rho, cfg.rho, cfg.sigma, 255).reshape(-1)
+        self.nb = data.size // (n * n)
+        self.x = torch.from_numpy(np.ascontiguousarray(data)).to(self.dev)
+        blocks = np.zeros(self.nb, dtype=_lib.BLOCK_DTYPE)
+        blocks["offset"] = np.arange(self.nb, dtype=np.int64) * n * n
+        blocks["w"] = blocks["h"] = n
+        if cfg.kind == 1:
+            self.theta = np.zeros(sum(len(_layer_pairs(n, p)) for p in cfg.parities))
+        else:
+            B = targets.core(n, cfg.core)
+            # start from the orthogonal Procrustes fit of the K x K block: Q = U V^T of D_K B_K^T
+            u, _, vt = np.linalg.svd(self.D[:cfg.k, :] @ B[:cfg.k, :].T)
+            self.w, self.dg = cayley_init(u @ vt)
+        self.plan = _lib.Plan([self._tf()])
+        self.plan.set_blocks(blocks, data.size)
+        self.lay = self.plan.param_layout()
+        self.y = torch.empty(data.size, dtype=torch.float32, device=self.dev)
+        self.gy = torch.empty_like(self.y)
+        self.gp = torch.zeros(max(1, self.lay[-1]), dtype=torch.float32, device=self.dev)
+        self.work = torch.zeros(65 * n * n, dtype=torch.float64, device=self.dev)
+        self.loss_dev = torch.zeros(1, dtype=torch.float64, device=self.dev)
+        self.m1 = self.m2 = None
+        self.t = 0
+
+    # current transform -------------------------------------------------------------
+    def q(self):
+        return cayley_q(self.w, self.cfg.k, self.dg)
+
+    def _tf(self):
+        c = self.cfg
+        if c.kind == 1:
+            return {"n": c.n, "core": c.core, "kind": 1, "parities": np.array(c.parities, np.uint8),
+                    "angles": self.theta}
+        return {"n": c.n, "core": c.core, "kind": 2, "q": self.q()}
+
+    def H(self):
+        c = self.cfg
+        if c.kind == 1:
+            return band_H(c.n, c.core, c.parities, self.theta)
+        C = np.eye(c.n)
+        C[:c.k, :c.k] = self.q()
+        return C @ targets.core(c.n, c.core)
+
+    # loss and gradient -------------------------------------------------------------
+    def basis_term(self):
+        c = self.cfg
+        H = self.H()
+        if c.eq2:
+            wts = np.exp(-math.log(100.0) / c.n * np.arange(c.n))[:, None]
+            diff = H - self.D
+            return float(np.sum(wts * diff ** 2)), 2.0 * wts * diff
+        diff = np.zeros_like(H)
+        diff[:c.m] = H[:c.m] - self.D[:c.m]
+        return float(np.sum(diff ** 2)), 2.0 * diff
+
+    def loss_and_grad(self):
+        """Loss and gradient w.r.t. the free parameters (theta, or the Cayley w)."""
+        c = self.cfg
+        torch = self.torch
+        lib = self.plan._lib
+        stream = torch.cuda.current_stream(self.dev)
+        self.plan.update_params([self._tf()])
+        self.plan.fwd(self.x, self.y, stream)
+        n2 = c.n * c.n
+        _lib.check(lib.adj_coding_gain_proxy(self.y.data_ptr(), self.nb, n2, self.work.data_ptr(),
+                                             self.loss_dev.data_ptr(), self.gy.data_ptr(), stream.cuda_stream))
+        # the backward is linear in dL/dY: the proxy gradient is scaled by lam on the host
+        self.plan.bwd(self.x, self.gy, None, self.gp, stream)
+        torch.cuda.synchronize(self.dev)
+        proxy = float(self.loss_dev.item())
+        g_proxy = self.gp[self.lay[0]:self.lay[1]].double().cpu().numpy()
+        basis, dH = self.basis_term()
+        loss = basis + c.lam * proxy
+        if c.kind == 1:
+            g = band_angle_grad(c.n, c.core, c.parities, self.theta, dH) + c.lam * g_proxy
+        else:
+            B = targets.core(c.n, c.core)
+            gq = (dH @ B.T)[:c.k, :c.k] + c.lam * g_proxy.reshape(c.k, c.k)
+            g = cayley_grad(self.w, c.k, self.dg, gq)
+        return loss, basis, proxy, g
+
+    def params(self):
+        return self.theta if self.cfg.kind == 1 else self.w
+
+    def set_params(self, v):
+        if self.cfg.kind == 1:
+            self.theta = np.asarray(v, dtype=np.float64)
+        else:
+            self.w = np.asarray(v, dtype=np.float64)
+
+    def step(self):
+        """One Adam step; returns the loss before it."""
+        loss, basis, proxy, g = self.loss_and_grad()
+        b1, b2, eps = 0.9, 0.999, 1e-12
+        if self.m1 is None:
+            self.m1 = np.zeros_like(g)
+            self.m2 = np.zeros_like(g)
+        self.t += 1
+        self.m1 = b1 * self.m1 + (1 - b1) * g
+        self.m2 = b2 * self.m2 + (1 - b2) * g * g
+        mh = self.m1 / (1 - b1 ** self.t)
+        vh = self.m2 / (1 - b2 ** self.t)
+        self.set_params(self.params() - self.cfg.lr * mh / (np.sqrt(vh) + eps))
+        self.cfg.history.append({"step": self.t, "loss": loss, "basis": basis, "proxy": proxy,
+                                 "grad_norm": float(np.linalg.norm(g))})
+        return loss
+
+    def run(self, steps=None, log_every=0):
+        for i in range(steps or self.cfg.steps):
+            loss = self.step()
+            if log_every and (i % log_every == 0):
+                print(f"step {self.t:4d} loss {loss:.6f}", flush=True)
+        return self.loss_and_grad()[0]
+
+    # checkpoint ------------------------------------------------------------------
+    def state(self):
+        c = self.cfg
+        d = {"config": {k: getattr(c, k) for k in ("n", "core", "kind", "parities", "k", "target", "m", "lam",
+                                                   "eq2", "blocks", "rho", "sigma", "seed", "lr")},
+             "step": self.t, "params": self.params().tolist(),
+             "adam": None if self.m1 is None else [self.m1.tolist(), self.m2.tolist()]}
+        if c.kind == 2:
+            d["dg"] = self.dg.tolist()
+            d["q"] = self.q().tolist()
+        else:
+            d["angles"] = self.theta.tolist()
+        d["history"] = c.history
+        return d
+
+    def save(self, path):
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(self.state(), f)
+
+    def load(self, path):
+        with open(path) as f:
+            d = json.load(f)
+        self.t = d["step"]
+        self.set_params(d["params"])
+        if self.cfg.kind == 2:
+            self.dg = np.array(d["dg"])
+        if d.get("adam"):
+            self.m1, self.m2 = (np.array(a) for a in d["adam"])
+        self.cfg.history = d.get("history", [])
+
+    def close(self):
+        self.plan.close()

@@ -34,3 +34,15 @@ def chessboard(q: np.ndarray) -> np.ndarray:
     q = np.asarray(q, dtype=np.float64)
     s = (-1.0) ** np.arange(q.shape[0])
     return q * s[:, None] * s[None, :]
+
+
+def core(n: int, kind: int) -> np.ndarray:
+    """The fast cores of Section 2.1 as dense FP64 matrices (0 DCT-2, 1 DCT-3, 2 DST-2,
+    3 DST-3), orthonormal; used by the fitter's host-side model of H."""
+    k = np.arange(n)[:, None]
+    m = np.arange(n)[None, :]
+    c2 = np.sqrt(2.0 / n) * np.cos(np.pi * (2 * m + 1) * k / (2 * n))
+    c2[0] /= np.sqrt(2.0)
+    s2 = np.sqrt(2.0 / n) * np.sin(np.pi * (2 * m + 1) * (k + 1) / (2 * n))
+    s2[n - 1] /= np.sqrt(2.0)
+    return {0: c2, 1: c2.T.copy(), 2: s2, 3: s2.T.copy()}[int(kind)]
