@@ -60,6 +60,22 @@ def workload(rank=0, frames=8):
     return synth.config3(seed=3 + 1000 * rank, frames=frames)
 
 
+def aggregate_max(t_local, device=None):
+    """Max of a per-rank time over all ranks (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t_local)
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, steps, t_max):
+    """Weak scaling: every rank processes units_per_rank per step; the job takes t_max."""
+    return units_per_rank * world * steps / t_max
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -261,12 +277,8 @@ def run_fused(args):
         torch.distributed.barrier()
     t_fwd = np.array([e[0].elapsed_time(e[1]) for e in events]) * 1e-3
     t_inv = np.array([e[2].elapsed_time(e[3]) for e in events]) * 1e-3
-    t_total = float(t_fwd.sum() + t_inv.sum())
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = coefs * world * args.steps / t_total / 1e9
+    t_total = aggregate_max(float(t_fwd.sum() + t_inv.sum()), dev)
+    value = whole_job_rate(coefs, world, args.steps, t_total) / 1e9
 
     # the plain (unfused) form on the same blocks, replayed from CUDA graphs (its best case:
     # no per-launch host overhead); same flushes and event timing as the fused kernels
@@ -309,12 +321,8 @@ def run_fused(args):
     for _ in range(args.e2e_steps):
         plan.fwd_host(h_x, h_y, stream)
         plan.inv_host(h_y, h_xr, stream)
-    e2e_t = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(tt.item())
-    e2e_value = coefs * world / e2e_t / 1e9
+    e2e_t = aggregate_max((time.perf_counter() - t0) / args.e2e_steps, dev)
+    e2e_value = whole_job_rate(coefs, world, 1, e2e_t) / 1e9
 
     # roofline of the dominant kernel (algorithmic bytes per launch / mean duration)
     nb = int(wl.blocks.size)

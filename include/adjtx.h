@@ -92,6 +92,16 @@ typedef struct {
 
 typedef struct adj_plan adj_plan_t;
 
+/* Launch and tiling choices of a plan (see adj_plan_autotune).
+ * cap_div[(log2 w - 2) * 5 + (log2 h - 2)]: a tile of w x h blocks holds 1/cap_div of the
+ * most that fit (1, 2, 4 or 8); ctas_per_sm: persistent CTAs per SM (0 = as many as fit);
+ * ranges_per_sm: scheduling ranges of the class-sorted tile list per SM (1..4). */
+typedef struct {
+  int32_t cap_div[25];
+  int32_t ctas_per_sm;
+  int32_t ranges_per_sm;
+} adj_tuning_t;
+
 /* Plan flags. */
 #define ADJ_PLAN_DEFAULT 0
 
@@ -232,6 +242,24 @@ int adj_graph_create(adj_plan_t* plan, int32_t what, const void* d_in, float* d_
                      adj_graph_t** graph);
 int adj_graph_launch(adj_graph_t* graph, void* stream);
 void adj_graph_destroy(adj_graph_t* graph);
+
+/* Read / replace a plan's tuning; replacing rebuilds its tile layout (no graph made from the
+ * plan may be launched afterwards).  Errors: INVALID_ARG (values out of range), CUDA. */
+int adj_plan_get_tuning(const adj_plan_t* plan, adj_tuning_t* tuning);
+int adj_plan_set_tuning(adj_plan_t* plan, const adj_tuning_t* tuning);
+
+/*
+ * Autotuner: times forward + inverse on the plan's own blocks (d_resid int16 input,
+ * d_coef and d_recon FP32 scratch of total_coefs samples, all device) for candidate
+ * tunings and keeps the fastest: CTAs per SM, ranges per SM, then the tile capacity of each
+ * block size in order of its share of the coefficients (coordinate descent).  If
+ * cache_path is given, a result stored there for this device and this workload signature
+ * (block sizes and transform kinds) is applied without measuring, and a new result is
+ * appended.  max_evals bounds the number of timed candidates (0: no bound).  Synchronises
+ * `stream`.  Errors: INVALID_ARG, NO_BLOCKS, MISALIGNED, CUDA.
+ */
+int adj_plan_autotune(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, float* d_recon,
+                      const char* cache_path, int32_t max_evals, void* stream);
 
 /* Launch geometry and tile statistics of a plan (for benchmarks and tests). */
 typedef struct {

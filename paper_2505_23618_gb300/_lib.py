@@ -31,7 +31,8 @@ EXPORTED = (
     "adj_transform_inv_host", "adj_plan_info", "adj_plan_destroy", "adj_last_error",
     "adj_transform_fwd_uniform_noalloc", "adj_transform_fwd_plain", "adj_transform_inv_plain",
     "adj_graph_create", "adj_graph_launch", "adj_graph_destroy", "adj_transform_bwd",
-    "adj_plan_param_layout", "adj_coding_gain_proxy",
+    "adj_plan_param_layout", "adj_coding_gain_proxy", "adj_plan_get_tuning", "adj_plan_set_tuning",
+    "adj_plan_autotune",
 )
 DTYPE_INT16, DTYPE_FP32 = 0, 1
 GRAPH_FWD, GRAPH_INV, GRAPH_FWD_PLAIN, GRAPH_INV_PLAIN, GRAPH_ROUNDTRIP = range(5)
@@ -42,6 +43,10 @@ class Adj1dDesc(C.Structure):
                 ("n_layers", C.c_int32), ("layer_parity", C.POINTER(C.c_uint8)),
                 ("angles", C.POINTER(C.c_double)), ("k", C.c_int32),
                 ("q", C.POINTER(C.c_double))]
+
+
+class AdjTuning(C.Structure):
+    _fields_ = [("cap_div", C.c_int32 * 25), ("ctas_per_sm", C.c_int32), ("ranges_per_sm", C.c_int32)]
 
 
 class AdjPlanInfo(C.Structure):
@@ -77,6 +82,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.adj_transform_bwd.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.adj_plan_param_layout.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.adj_coding_gain_proxy.argtypes = [vp, i64, i32, vp, vp, vp, vp]
+    lib.adj_plan_get_tuning.argtypes = [vp, C.POINTER(AdjTuning)]
+    lib.adj_plan_set_tuning.argtypes = [vp, C.POINTER(AdjTuning)]
+    lib.adj_plan_autotune.argtypes = [vp, vp, vp, vp, C.c_char_p, i32, vp]
     lib.adj_graph_create.argtypes = [vp, i32, vp, vp, vp, C.POINTER(vp)]
     lib.adj_graph_launch.argtypes = [vp, vp]
     lib.adj_graph_destroy.argtypes = [vp]
@@ -204,6 +212,25 @@ class Plan:
             x_fp32 = getattr(d_x, "dtype", None) is not None and "float" in str(d_x.dtype)
         check(self._lib.adj_transform_bwd(self._h, _ptr(d_x), DTYPE_FP32 if x_fp32 else DTYPE_INT16,
                                           _ptr(d_gy), _ptr(d_gx), _ptr(d_gparams), _stream(stream)))
+
+    def tuning(self) -> dict:
+        t = AdjTuning()
+        check(self._lib.adj_plan_get_tuning(self._h, C.byref(t)))
+        return {"cap_div": list(t.cap_div), "ctas_per_sm": t.ctas_per_sm, "ranges_per_sm": t.ranges_per_sm}
+
+    def set_tuning(self, tuning: dict):
+        t = AdjTuning()
+        t.cap_div[:] = list(tuning["cap_div"])
+        t.ctas_per_sm = int(tuning["ctas_per_sm"])
+        t.ranges_per_sm = int(tuning["ranges_per_sm"])
+        check(self._lib.adj_plan_set_tuning(self._h, C.byref(t)))
+
+    def autotune(self, d_in, d_coef, d_recon, cache_path=None, max_evals=0, stream=None):
+        """Time candidate tunings on this plan's blocks and keep the fastest (see the header)."""
+        path = cache_path.encode() if cache_path else None
+        check(self._lib.adj_plan_autotune(self._h, _ptr(d_in), _ptr(d_coef), _ptr(d_recon), path,
+                                          int(max_evals), _stream(stream)))
+        return self.tuning()
 
     def param_layout(self):
         """Offsets of each transform's gradient entries (n_tfs + 1 values)."""

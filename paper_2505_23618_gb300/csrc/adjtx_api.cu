@@ -83,6 +83,9 @@ struct adj_plan {
   float* d_partial = nullptr;
   double* d_M = nullptr;
   int bwd_grid = 0;
+  std::vector<adj_block_t> blocks;     // validated, in storage order
+  adj_tuning_t tuning{};
+  int occ_fwd = 0, occ_inv = 0;        // resident CTAs per SM of the fused kernels
 };
 
 namespace {
@@ -322,6 +325,134 @@ int run_host(adj_plan* p, bool inverse, const void* h_in, float* h_out, cudaStre
 
 }  // namespace
 
+int tuned_capacity(const adj_plan* p, int w, int h) {
+  const int cls = (ilog2(w) - 2) * 5 + (ilog2(h) - 2);
+  const int div = std::max(1, p->tuning.cap_div[cls]);
+  return std::max(1, tile_capacity(w, h) / div);
+}
+
+void apply_grid(adj_plan* p) {
+  const int c = p->tuning.ctas_per_sm;
+  p->grid_fwd = std::max(1, c > 0 ? std::min(c, p->occ_fwd) : p->occ_fwd) * p->n_sm;
+  p->grid_inv = std::max(1, c > 0 ? std::min(c, p->occ_inv) : p->occ_inv) * p->n_sm;
+}
+
+// Tiles, per-SM ranges and the plain form's per-size lists for the plan's block list,
+// under the plan's tuning.
+int build_layout(adj_plan* p) {
+  // Tiles: blocks of one (w, h, tf_h, tf_v) class, filled in storage order, then listed
+  // class by class so that consecutive tiles run the same code: the order is by block size,
+  // then by the code-determining (core, kind) of each direction, then by transform index.
+  struct Open {
+    std::vector<uint32_t> offs;
+    int64_t first;
+  };
+  std::unordered_map<uint64_t, Open> open;
+  struct Done {
+    uint64_t key;
+    int64_t first;
+    TileDev t;
+    std::vector<uint32_t> offs;
+  };
+  std::vector<Done> done;
+  auto emit = [&](uint64_t key, Open& o) {
+    Done d;
+    d.key = key;
+    d.first = o.first;
+    d.t = TileDev{};
+    d.t.w = (uint16_t)(key >> 48);
+    d.t.h = (uint16_t)(key >> 32);
+    d.t.tf_h = (uint16_t)(key >> 16);
+    d.t.tf_v = (uint16_t)key;
+    d.t.nblk = (uint16_t)o.offs.size();
+    d.offs.swap(o.offs);
+    done.push_back(std::move(d));
+  };
+  for (const adj_block_t& b : p->blocks) {
+    const uint64_t key = ((uint64_t)b.w << 48) | ((uint64_t)b.h << 32) | ((uint64_t)b.tf_h << 16) | b.tf_v;
+    Open& o = open[key];
+    if (o.offs.empty()) o.first = b.offset;
+    o.offs.push_back((uint32_t)(b.offset / 16));
+    if ((int)o.offs.size() >= tuned_capacity(p, b.w, b.h)) emit(key, o);
+  }
+  for (auto& kv : open)
+    if (!kv.second.offs.empty()) emit(kv.first, kv.second);
+  auto code_key = [&](const Done& d) {
+    const TfHost &th = p->tfs[d.t.tf_h], &tv = p->tfs[d.t.tf_v];
+    return ((uint64_t)d.t.w << 40) | ((uint64_t)d.t.h << 32) | ((uint64_t)th.kind << 28) |
+           ((uint64_t)th.core << 24) | ((uint64_t)tv.kind << 20) | ((uint64_t)tv.core << 16);
+  };
+  std::stable_sort(done.begin(), done.end(), [&](const Done& a, const Done& b) {
+    const uint64_t ka = code_key(a), kb = code_key(b);
+    if (ka != kb) return ka < kb;
+    return a.key != b.key ? a.key < b.key : a.first < b.first;
+  });
+  std::vector<TileDev> tiles;
+  std::vector<uint32_t> tblk;
+  tiles.reserve(done.size());
+  tblk.reserve(p->blocks.size());
+  // Each tile's block list starts on a 16-byte boundary and the list ends with 4 spare
+  // entries: the kernel fetches a tile's offsets with 16-byte asynchronous copies.
+  for (Done& d : done) {
+    while (tblk.size() % 4) tblk.push_back(0u);
+    d.t.blk_begin = (uint32_t)tblk.size();
+    tiles.push_back(d.t);
+    tblk.insert(tblk.end(), d.offs.begin(), d.offs.end());
+  }
+  tblk.resize(tblk.size() + 4, 0u);
+
+  // Per-SM ranges of the sorted tile list with about equal numbers of coefficients.
+  const int n_ranges = tiles.empty() ? 0 : (int)std::min<size_t>({(size_t)std::max(1, p->n_sm * std::max(1, p->tuning.ranges_per_sm)), (size_t)kMaxRanges, tiles.size()});
+  std::vector<unsigned> rbeg;
+  if (n_ranges > 0) {
+    std::vector<int64_t> cum(tiles.size() + 1, 0);
+    for (size_t i = 0; i < tiles.size(); ++i) cum[i + 1] = cum[i] + (int64_t)tiles[i].nblk * tiles[i].w * tiles[i].h;
+    rbeg.push_back(0);
+    for (int r = 1; r < n_ranges; ++r) {
+      const int64_t target = cum.back() * r / n_ranges;
+      size_t i = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
+      i = std::max<size_t>(i, rbeg.back());
+      rbeg.push_back((unsigned)std::min(i, tiles.size()));
+    }
+    rbeg.push_back((unsigned)tiles.size());
+  }
+
+  // Plain form: blocks grouped by size, in storage order within a size.
+  std::vector<PlainBlock> pblk;
+  std::vector<PlainClass> pcls;
+  for (int lw = 2; lw <= 6; ++lw)
+    for (int lh = 2; lh <= 6; ++lh) {
+      PlainClass c{1 << lw, 1 << lh, 0, nullptr};
+      const size_t first = pblk.size();
+      for (const adj_block_t& b : p->blocks) {
+        if (b.w == c.w && b.h == c.h) pblk.push_back(PlainBlock{(uint32_t)(b.offset / 16), b.tf_h, b.tf_v});
+      }
+      c.n_blocks = (int)(pblk.size() - first);
+      c.blocks = reinterpret_cast<const PlainBlock*>(first);  // index for now, pointer after upload
+      if (c.n_blocks) pcls.push_back(c);
+    }
+
+  free_blocks(p);
+  if (!pblk.empty()) {
+    CUDA_TRY(cudaMalloc(&p->d_plain, pblk.size() * sizeof(PlainBlock)));
+    CUDA_TRY(cudaMemcpy(p->d_plain, pblk.data(), pblk.size() * sizeof(PlainBlock), cudaMemcpyHostToDevice));
+    for (PlainClass& c : pcls) c.blocks = p->d_plain + reinterpret_cast<size_t>(c.blocks);
+  }
+  p->plain = pcls;
+  if (!tiles.empty()) {
+    CUDA_TRY(cudaMalloc(&p->d_tiles, tiles.size() * sizeof(TileDev)));
+    CUDA_TRY(cudaMalloc(&p->d_tile_blk, tblk.size() * sizeof(uint32_t)));
+    CUDA_TRY(cudaMalloc(&p->d_range_begin, rbeg.size() * sizeof(unsigned)));
+    CUDA_TRY(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p->d_tile_blk, tblk.data(), tblk.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p->d_range_begin, rbeg.data(), rbeg.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+  }
+  p->n_ranges = n_ranges;
+  p->n_tiles = (int)tiles.size();
+  p->has_blocks = true;
+  return ADJ_OK;
+}
+
 extern "C" {
 
 const char* adj_last_error(void) { return g_err.c_str(); }
@@ -449,7 +580,13 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     int occ = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
     if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
-    else (inv ? p->grid_inv : p->grid_fwd) = std::max(1, occ) * p->n_sm;
+    else (inv ? p->occ_inv : p->occ_fwd) = std::max(1, occ);
+  }
+  if (!rc) {
+    for (int i = 0; i < 25; ++i) p->tuning.cap_div[i] = 1;
+    p->tuning.ctas_per_sm = 0;
+    p->tuning.ranges_per_sm = 1;
+    apply_grid(p);
   }
   if (rc) {
     adj_plan_destroy(p);
@@ -503,119 +640,13 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
     if (a.offset + (int64_t)a.w * a.h > b.offset) return fail(ADJ_ERR_INVALID_ARG, "blocks %lld and %lld overlap", (long long)order[i - 1], (long long)order[i]);
   }
 
-  // Tiles: blocks of one (w, h, tf_h, tf_v) class, filled in storage order, then listed
-  // class by class so that consecutive tiles run the same code: the order is by block size,
-  // then by the code-determining (core, kind) of each direction, then by transform index.
-  struct Open {
-    std::vector<uint32_t> offs;
-    int64_t first;
-  };
-  std::unordered_map<uint64_t, Open> open;
-  struct Done {
-    uint64_t key;
-    int64_t first;
-    TileDev t;
-    std::vector<uint32_t> offs;
-  };
-  std::vector<Done> done;
-  auto emit = [&](uint64_t key, Open& o) {
-    Done d;
-    d.key = key;
-    d.first = o.first;
-    d.t = TileDev{};
-    d.t.w = (uint16_t)(key >> 48);
-    d.t.h = (uint16_t)(key >> 32);
-    d.t.tf_h = (uint16_t)(key >> 16);
-    d.t.tf_v = (uint16_t)key;
-    d.t.nblk = (uint16_t)o.offs.size();
-    d.offs.swap(o.offs);
-    done.push_back(std::move(d));
-  };
-  for (int64_t i : order) {
-    const adj_block_t& b = blocks[i];
-    const uint64_t key = ((uint64_t)b.w << 48) | ((uint64_t)b.h << 32) | ((uint64_t)b.tf_h << 16) | b.tf_v;
-    Open& o = open[key];
-    if (o.offs.empty()) o.first = b.offset;
-    o.offs.push_back((uint32_t)(b.offset / 16));
-    if ((int)o.offs.size() >= tile_capacity(b.w, b.h)) emit(key, o);
-  }
-  for (auto& kv : open)
-    if (!kv.second.offs.empty()) emit(kv.first, kv.second);
-  auto code_key = [&](const Done& d) {
-    const TfHost &th = p->tfs[d.t.tf_h], &tv = p->tfs[d.t.tf_v];
-    return ((uint64_t)d.t.w << 40) | ((uint64_t)d.t.h << 32) | ((uint64_t)th.kind << 28) |
-           ((uint64_t)th.core << 24) | ((uint64_t)tv.kind << 20) | ((uint64_t)tv.core << 16);
-  };
-  std::stable_sort(done.begin(), done.end(), [&](const Done& a, const Done& b) {
-    const uint64_t ka = code_key(a), kb = code_key(b);
-    if (ka != kb) return ka < kb;
-    return a.key != b.key ? a.key < b.key : a.first < b.first;
-  });
-  std::vector<TileDev> tiles;
-  std::vector<uint32_t> tblk;
-  tiles.reserve(done.size());
-  tblk.reserve(n_blocks);
-  // Each tile's block list starts on a 16-byte boundary and the list ends with 4 spare
-  // entries: the kernel fetches a tile's offsets with 16-byte asynchronous copies.
-  for (Done& d : done) {
-    while (tblk.size() % 4) tblk.push_back(0u);
-    d.t.blk_begin = (uint32_t)tblk.size();
-    tiles.push_back(d.t);
-    tblk.insert(tblk.end(), d.offs.begin(), d.offs.end());
-  }
-  tblk.resize(tblk.size() + 4, 0u);
-
-  // Per-SM ranges of the sorted tile list with about equal numbers of coefficients.
-  const int n_ranges = tiles.empty() ? 0 : (int)std::min<size_t>({(size_t)std::max(1, p->n_sm), (size_t)kMaxRanges, tiles.size()});
-  std::vector<unsigned> rbeg;
-  if (n_ranges > 0) {
-    std::vector<int64_t> cum(tiles.size() + 1, 0);
-    for (size_t i = 0; i < tiles.size(); ++i) cum[i + 1] = cum[i] + (int64_t)tiles[i].nblk * tiles[i].w * tiles[i].h;
-    rbeg.push_back(0);
-    for (int r = 1; r < n_ranges; ++r) {
-      const int64_t target = cum.back() * r / n_ranges;
-      size_t i = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
-      i = std::max<size_t>(i, rbeg.back());
-      rbeg.push_back((unsigned)std::min(i, tiles.size()));
-    }
-    rbeg.push_back((unsigned)tiles.size());
-  }
-
-  // Plain form: blocks grouped by size, in storage order within a size.
-  std::vector<PlainBlock> pblk;
-  std::vector<PlainClass> pcls;
-  for (int lw = 2; lw <= 6; ++lw)
-    for (int lh = 2; lh <= 6; ++lh) {
-      PlainClass c{1 << lw, 1 << lh, 0, nullptr};
-      const size_t first = pblk.size();
-      for (int64_t i : order) {
-        const adj_block_t& b = blocks[i];
-        if (b.w == c.w && b.h == c.h) pblk.push_back(PlainBlock{(uint32_t)(b.offset / 16), b.tf_h, b.tf_v});
-      }
-      c.n_blocks = (int)(pblk.size() - first);
-      c.blocks = reinterpret_cast<const PlainBlock*>(first);  // index for now, pointer after upload
-      if (c.n_blocks) pcls.push_back(c);
-    }
-
-  free_blocks(p);
-  if (!pblk.empty()) {
-    CUDA_TRY(cudaMalloc(&p->d_plain, pblk.size() * sizeof(PlainBlock)));
-    CUDA_TRY(cudaMemcpy(p->d_plain, pblk.data(), pblk.size() * sizeof(PlainBlock), cudaMemcpyHostToDevice));
-    for (PlainClass& c : pcls) c.blocks = p->d_plain + reinterpret_cast<size_t>(c.blocks);
-  }
-  p->plain = pcls;
-  if (!tiles.empty()) {
-    CUDA_TRY(cudaMalloc(&p->d_tiles, tiles.size() * sizeof(TileDev)));
-    CUDA_TRY(cudaMalloc(&p->d_tile_blk, tblk.size() * sizeof(uint32_t)));
-    CUDA_TRY(cudaMalloc(&p->d_range_begin, rbeg.size() * sizeof(unsigned)));
-    CUDA_TRY(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(p->d_tile_blk, tblk.data(), tblk.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(p->d_range_begin, rbeg.data(), rbeg.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
-  }
-  p->n_ranges = n_ranges;
-  p->n_tiles = (int)tiles.size();
+  p->blocks.clear();
+  p->blocks.reserve(n_blocks);
+  for (int64_t i : order) p->blocks.push_back(blocks[i]);
   p->n_blocks = n_blocks;
   p->total = total_coefs;
+  const int rc = build_layout(p);
+  if (rc) return rc;
   p->has_blocks = true;
   return ADJ_OK;
 }
@@ -662,6 +693,186 @@ int adj_transform_fwd_host(adj_plan_t* p, const int16_t* h_resid, float* h_coef,
 int adj_transform_inv_host(adj_plan_t* p, const float* h_coef, float* h_resid_out, void* stream) {
   g_err.clear();
   return run_host(p, true, h_coef, h_resid_out, static_cast<cudaStream_t>(stream));
+}
+
+int adj_plan_get_tuning(const adj_plan_t* p, adj_tuning_t* t) {
+  g_err.clear();
+  if (!p || !t) return fail(ADJ_ERR_INVALID_ARG, "null argument");
+  *t = p->tuning;
+  return ADJ_OK;
+}
+
+int adj_plan_set_tuning(adj_plan_t* p, const adj_tuning_t* t) {
+  g_err.clear();
+  if (!p || !t) return fail(ADJ_ERR_INVALID_ARG, "null argument");
+  for (int i = 0; i < 25; ++i)
+    if (t->cap_div[i] != 1 && t->cap_div[i] != 2 && t->cap_div[i] != 4 && t->cap_div[i] != 8)
+      return fail(ADJ_ERR_INVALID_ARG, "cap_div[%d] = %d", i, t->cap_div[i]);
+  if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return fail(ADJ_ERR_INVALID_ARG, "ctas_per_sm %d", t->ctas_per_sm);
+  if (t->ranges_per_sm < 1 || t->ranges_per_sm > 4) return fail(ADJ_ERR_INVALID_ARG, "ranges_per_sm %d", t->ranges_per_sm);
+  p->tuning = *t;
+  apply_grid(p);
+  if (p->has_blocks) return build_layout(p);
+  return ADJ_OK;
+}
+
+namespace {
+
+// FNV-1a over the block-size / transform-kind histogram: the workload signature of a tuning.
+uint64_t signature(const adj_plan* p) {
+  std::vector<uint64_t> hist(25 * 16, 0);
+  for (const adj_block_t& b : p->blocks) {
+    const int cls = (ilog2(b.w) - 2) * 5 + (ilog2(b.h) - 2);
+    hist[cls * 16 + p->tfs[b.tf_h].kind * 4 + p->tfs[b.tf_v].kind] += 1;
+  }
+  uint64_t h = 1469598103934665603ull;
+  for (uint64_t v : hist) {
+    // quantise counts to ~3% so that equal workloads of other seeds share a tuning
+    uint64_t q = v;
+    while (q >= 64) q = (q >> 1) | 0;  // keep the top bits
+    uint64_t lg = 0;
+    for (uint64_t t = v; t >= 64; t >>= 1) ++lg;
+    const uint64_t key = (lg << 8) | q;
+    for (int i = 0; i < 8; ++i) {
+      h ^= (key >> (8 * i)) & 0xff;
+      h *= 1099511628211ull;
+    }
+  }
+  return h;
+}
+
+std::string device_name(int dev) {
+  cudaDeviceProp prop{};
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+  std::string s = prop.name;
+  for (char& c : s)
+    if (c == ' ' || c == '"') c = '_';
+  return s;
+}
+
+// Cache lines: "<device> <signature hex> <ctas> <ranges> <25 cap_div>"
+bool cache_lookup(const char* path, const std::string& dev, uint64_t sig, adj_tuning_t* t) {
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char name[256];
+  unsigned long long s;
+  adj_tuning_t c{};
+  bool found = false;
+  while (fscanf(f, "%255s %llx %d %d", name, &s, &c.ctas_per_sm, &c.ranges_per_sm) == 4) {
+    bool ok = true;
+    for (int i = 0; i < 25 && ok; ++i) ok = fscanf(f, "%d", &c.cap_div[i]) == 1;
+    if (!ok) break;
+    if (dev == name && s == sig) {
+      *t = c;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& dev, uint64_t sig, const adj_tuning_t& t) {
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %llx %d %d", dev.c_str(), (unsigned long long)sig, t.ctas_per_sm, t.ranges_per_sm);
+  for (int i = 0; i < 25; ++i) fprintf(f, " %d", t.cap_div[i]);
+  fprintf(f, "\n");
+  fclose(f);
+}
+
+// median forward + inverse time (ms) of the plan as tuned now
+int time_plan(adj_plan* p, const int16_t* x, float* y, float* xr, cudaStream_t s, float* ms) {
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best[5];
+  int rc = run(p, false, x, y, s);
+  if (!rc) rc = run(p, true, y, xr, s);
+  for (int r = 0; r < 5 && !rc; ++r) {
+    cudaEventRecord(e0, s);
+    rc = run(p, false, x, y, s);
+    if (!rc) rc = run(p, true, y, xr, s);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
+    if (!rc) cudaEventElapsedTime(&best[r], e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  std::sort(best, best + 5);
+  *ms = best[2];
+  return ADJ_OK;
+}
+
+}  // namespace
+
+int adj_plan_autotune(adj_plan_t* p, const int16_t* x, float* y, float* xr, const char* cache_path, int32_t max_evals,
+                      void* stream_) {
+  g_err.clear();
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  int rc;
+  if ((rc = check_ptr(x, "input")) || (rc = check_ptr(y, "coefficients")) || (rc = check_ptr(xr, "reconstruction")))
+    return rc;
+  if (p->n_tiles == 0) return ADJ_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream_);
+  const std::string dev = device_name(p->device);
+  const uint64_t sig = signature(p);
+  adj_tuning_t t{};
+  if (cache_lookup(cache_path, dev, sig, &t)) return adj_plan_set_tuning(p, &t);
+
+  int evals = 0;
+  auto budget = [&]() { return max_evals <= 0 || evals < max_evals; };
+  adj_tuning_t best = p->tuning;
+  float best_ms = 0.f;
+  if ((rc = time_plan(p, x, y, xr, s, &best_ms))) return rc;
+  auto trial = [&](const adj_tuning_t& cand) -> int {
+    if (!budget()) return ADJ_OK;
+    ++evals;
+    int r = adj_plan_set_tuning(p, &cand);
+    float ms = 0.f;
+    if (!r) r = time_plan(p, x, y, xr, s, &ms);
+    if (r) return r;
+    if (ms < best_ms * 0.99f) {
+      best_ms = ms;
+      best = cand;
+    }
+    return ADJ_OK;
+  };
+  // persistent CTAs per SM, then ranges per SM
+  const int occ = std::min(p->occ_fwd, p->occ_inv);
+  for (int c = occ - 1; c >= std::max(2, occ - 2); --c) {
+    adj_tuning_t cand = best;
+    cand.ctas_per_sm = c;
+    if ((rc = trial(cand))) return rc;
+  }
+  for (int r = 2; r <= 4; r *= 2) {
+    adj_tuning_t cand = best;
+    cand.ranges_per_sm = r;
+    if ((rc = trial(cand))) return rc;
+  }
+  // tile capacity per block size, largest coefficient shares first
+  std::vector<std::pair<int64_t, int>> share(25);
+  for (int i = 0; i < 25; ++i) share[i] = {0, i};
+  for (const adj_block_t& b : p->blocks) share[(ilog2(b.w) - 2) * 5 + (ilog2(b.h) - 2)].first += (int64_t)b.w * b.h;
+  std::sort(share.rbegin(), share.rend());
+  for (const auto& sc : share) {
+    if (sc.first == 0) break;
+    const int cls = sc.second;
+    const int w = 4 << (cls / 5), h = 4 << (cls % 5);
+    for (int div = 2; div <= 8; div *= 2) {
+      if (tile_capacity(w, h) / div < 1) break;
+      adj_tuning_t cand = best;
+      cand.cap_div[cls] = div;
+      if ((rc = trial(cand))) return rc;
+    }
+  }
+  if ((rc = adj_plan_set_tuning(p, &best))) return rc;
+  cache_store(cache_path, dev, sig, best);
+  return ADJ_OK;
 }
 
 int adj_plan_info(const adj_plan_t* p, adj_plan_info_t* info) {

@@ -100,3 +100,26 @@ def test_graph_replay_matches_direct_calls():
         assert torch.equal(gy, y) and torch.equal(gx, xr)
         assert float((gpi_out - x.float()).abs().max()) <= 1e-2
         g.close(), gp.close(), gpi.close()
+
+
+def test_autotune_and_tuning_roundtrip(tmp_path):
+    """The autotuner picks a tuning that keeps results identical; the cache replays it."""
+    import torch
+    import paper_2505_23618_gb300 as adj
+    wl = synth.config3(frames=1, width=1280, height=720)
+    with adj.Plan(wl.tfs) as plan:
+        plan.set_blocks(wl.blocks, wl.total)
+        x = torch.from_numpy(wl.data).cuda()
+        y0, xr0 = adj.roundtrip(plan, x)
+        y = torch.zeros_like(y0)
+        xr = torch.zeros_like(y0)
+        cache = str(tmp_path / "tune.txt")
+        t = plan.autotune(x, y, xr, cache_path=cache, max_evals=12)
+        y1, xr1 = adj.roundtrip(plan, x)
+        torch.cuda.synchronize()
+        # tiling changes only which CTA transforms a block, not the arithmetic
+        assert torch.equal(y1, y0) and torch.equal(xr1, xr0)
+        plan.set_tuning({"cap_div": [1] * 25, "ctas_per_sm": 0, "ranges_per_sm": 1})
+        assert plan.autotune(x, y, xr, cache_path=cache) == t
+        with pytest.raises(adj.AdjError):
+            plan.set_tuning({"cap_div": [3] * 25, "ctas_per_sm": 0, "ranges_per_sm": 1})
