@@ -11,11 +11,21 @@
 namespace adjtx {
 
 // ---------------------------------------------------------------------------------
+// Element types.  T = float: one line per thread.  T = float2: two lines per thread,
+// element j of line 0 in .x and of line 1 in .y, processed by the packed FP32x2
+// instructions (one instruction per operation for both lines).  Runtime coefficients of a
+// packed line pair come from duplicated tables ({c, c, s, s} per rotation, {q, q} per Q
+// entry) so that they load as ready-made pairs.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float vmulv(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 vmulv(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// ---------------------------------------------------------------------------------
 // Fast cores (Section 2.1).  Cores 0..3 are DCT-2, DCT-3, DST-2, DST-3; the inverse of
 // each is its transpose, which is the core with index c ^ 1.
 // ---------------------------------------------------------------------------------
-template <int N>
-__device__ __forceinline__ void core_apply(int core, float (&v)[N]) {
+template <int N, class T>
+__device__ __forceinline__ void core_apply(int core, T (&v)[N]) {
   switch (core) {
     case 0: Core<N, 0>::apply(v); break;
     case 1: Core<N, 1>::apply(v); break;
@@ -29,19 +39,31 @@ __device__ __forceinline__ void core_apply(int core, float (&v)[N]) {
 // Forward: layer 0 first, (x_i, x_{i+1}) -> (c x_i - s x_{i+1}, s x_i + c x_{i+1}).
 // Inverse (A^T): last layer first, each rotation transposed.
 // ---------------------------------------------------------------------------------
-template <int N, int PAR, bool INV>
-__device__ __forceinline__ void rot_layer(float (&v)[N], const float2* __restrict__ cs) {
+__device__ __forceinline__ void load_cs(const float* P, const TfDev& tf, int idx, float& c, float& s) {
+  const float2 t = __ldg(reinterpret_cast<const float2*>(P) + tf.cs_off + idx);
+  c = t.x;
+  s = t.y;
+}
+__device__ __forceinline__ void load_cs(const float* P, const TfDev& tf, int idx, float2& c, float2& s) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(P) + tf.cs2_off + idx);
+  c = make_float2(t.x, t.y);
+  s = make_float2(t.z, t.w);
+}
+
+template <int N, int PAR, bool INV, class T>
+__device__ __forceinline__ void rot_layer(T (&v)[N], const TfDev& tf, const float* __restrict__ P, int off) {
 #pragma unroll
   for (int p = 0; p < (N - PAR) / 2; ++p) {
     const int i = 2 * p + PAR;
-    const float2 t = __ldg(cs + p);
-    const float x = v[i], y = v[i + 1];
+    T c, s;
+    load_cs(P, tf, off + p, c, s);
+    const T x = v[i], y = v[i + 1];
     if (!INV) {
-      v[i] = t.x * x - t.y * y;
-      v[i + 1] = t.y * x + t.x * y;
+      v[i] = vfma(c, x, vneg(vmulv(s, y)));
+      v[i + 1] = vfma(c, y, vmulv(s, x));
     } else {
-      v[i] = t.x * x + t.y * y;
-      v[i + 1] = t.x * y - t.y * x;
+      v[i] = vfma(c, x, vmulv(s, y));
+      v[i + 1] = vfma(c, y, vneg(vmulv(s, x)));
     }
   }
 }
@@ -50,17 +72,16 @@ __device__ __forceinline__ int layer_parity(const TfDev& tf, int l) {
   return l < 32 ? (tf.par_lo >> l) & 1 : (tf.par_hi >> (l - 32)) & 1;
 }
 
-template <int N, bool INV>
-__device__ __forceinline__ void band(float (&v)[N], const TfDev& tf, const float* __restrict__ P) {
-  const float2* cs = reinterpret_cast<const float2*>(P) + tf.cs_off;
+template <int N, bool INV, class T>
+__device__ __forceinline__ void band(T (&v)[N], const TfDev& tf, const float* __restrict__ P) {
   if (!INV) {
     int off = 0;
     for (int l = 0; l < tf.n_layers; ++l) {
       if (layer_parity(tf, l) == 0) {
-        rot_layer<N, 0, false>(v, cs + off);
+        rot_layer<N, 0, false>(v, tf, P, off);
         off += N / 2;
       } else {
-        rot_layer<N, 1, false>(v, cs + off);
+        rot_layer<N, 1, false>(v, tf, P, off);
         off += N / 2 - 1;
       }
     }
@@ -69,10 +90,10 @@ __device__ __forceinline__ void band(float (&v)[N], const TfDev& tf, const float
     for (int l = tf.n_layers - 1; l >= 0; --l) {
       if (layer_parity(tf, l) == 0) {
         off -= N / 2;
-        rot_layer<N, 0, true>(v, cs + off);
+        rot_layer<N, 0, true>(v, tf, P, off);
       } else {
         off -= N / 2 - 1;
-        rot_layer<N, 1, true>(v, cs + off);
+        rot_layer<N, 1, true>(v, tf, P, off);
       }
     }
   }
@@ -81,38 +102,49 @@ __device__ __forceinline__ void band(float (&v)[N], const TfDev& tf, const float
 // ---------------------------------------------------------------------------------
 // Post-adjustment C = diag(Q, I): the padded KT x KT block Qp = diag(Q, I_{KT-K}) (row
 // major) acts on the first KT outputs.  Forward: y_i = sum_j Qp[i][j] u_j, written out
-// directly at runtime index i (four rows per step, independent accumulators).
+// directly at runtime index i (several rows per step, independent accumulators).
 // Inverse (C^T): u_j = sum_i Qp[i][j] y_i with y_i read back from the source line.
+// Four consecutive entries of a Q row load as one float4 (scalar lines) or two {q, q}
+// pairs (packed lines).
 // ---------------------------------------------------------------------------------
 // Rows of Qp handled per step: enough independent accumulators for ILP while the Q
 // loads the compiler hoists out of the unrolled dot product still fit in registers.
-template <int KT>
+template <int KT, class T>
 struct PostRows {
-  static constexpr int R = KT >= 64 ? 1 : (KT >= 32 ? 2 : 4);
+  static constexpr int R = sizeof(T) == 8 ? (KT >= 32 ? 1 : 2) : (KT >= 64 ? 1 : (KT >= 32 ? 2 : 4));
 };
 
-template <int N, int KT, class Dst>
-__device__ __forceinline__ void post_fwd_k(const float (&v)[N], const float* __restrict__ Q,
+// Qp[i][4g .. 4g+3] as element-type coefficients
+__device__ __forceinline__ void q_quad(const float* P, const TfDev& tf, int i, int g, float (&q)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(P + tf.q_off + i * tf.kt) + g);
+  q[0] = t.x; q[1] = t.y; q[2] = t.z; q[3] = t.w;
+}
+__device__ __forceinline__ void q_quad(const float* P, const TfDev& tf, int i, int g, float2 (&q)[4]) {
+  const float4* base = reinterpret_cast<const float4*>(P + tf.q2_off + 2 * i * tf.kt) + 2 * g;
+  const float4 a = __ldg(base), b = __ldg(base + 1);
+  q[0] = make_float2(a.x, a.y); q[1] = make_float2(a.z, a.w);
+  q[2] = make_float2(b.x, b.y); q[3] = make_float2(b.z, b.w);
+}
+
+template <int N, int KT, class T, class Dst>
+__device__ __forceinline__ void post_fwd_k(const T (&v)[N], const TfDev& tf, const float* __restrict__ P,
                                            const Dst& dst) {
-  constexpr int R = PostRows<KT>::R;
+  constexpr int R = PostRows<KT, T>::R;
 #pragma unroll
   for (int i = KT; i < N; ++i) dst.put(i, v[i]);
 #pragma unroll 1
   for (int i = 0; i < KT; i += R) {
-    const float4* q = reinterpret_cast<const float4*>(Q + i * KT);
-    float acc[R];
+    T acc[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = 0.f;
+    for (int r = 0; r < R; ++r) acc[r] = vzero(v[0]);
 #pragma unroll
-    for (int j = 0; j < KT / 4; ++j) {
-      const float u0 = v[4 * j], u1 = v[4 * j + 1], u2 = v[4 * j + 2], u3 = v[4 * j + 3];
+    for (int g = 0; g < KT / 4; ++g) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float4 c = __ldg(q + r * (KT / 4) + j);
-        acc[r] = fmaf(c.x, u0, acc[r]);
-        acc[r] = fmaf(c.y, u1, acc[r]);
-        acc[r] = fmaf(c.z, u2, acc[r]);
-        acc[r] = fmaf(c.w, u3, acc[r]);
+        T q[4];
+        q_quad(P, tf, i + r, g, q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[r] = vfma(q[e], v[4 * g + e], acc[r]);
       }
     }
 #pragma unroll
@@ -120,54 +152,49 @@ __device__ __forceinline__ void post_fwd_k(const float (&v)[N], const float* __r
   }
 }
 
-template <int N, int KT, class Src>
-__device__ __forceinline__ void post_inv_k(float (&v)[N], const float* __restrict__ Q, const Src& src) {
-  constexpr int R = PostRows<KT>::R;
+template <int N, int KT, class T, class Src>
+__device__ __forceinline__ void post_inv_k(T (&v)[N], const TfDev& tf, const float* __restrict__ P, const Src& src) {
+  constexpr int R = PostRows<KT, T>::R;
 #pragma unroll
-  for (int j = 0; j < KT; ++j) v[j] = 0.f;
+  for (int j = 0; j < KT; ++j) v[j] = vzero(v[0]);
 #pragma unroll 1
   for (int i = 0; i < KT; i += R) {
-    float y[R];
+    T y[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) y[r] = src.get_rt(i + r);
-    const float4* q = reinterpret_cast<const float4*>(Q + i * KT);
 #pragma unroll
-    for (int j = 0; j < KT / 4; ++j) {
+    for (int g = 0; g < KT / 4; ++g) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float4 c = __ldg(q + r * (KT / 4) + j);
-        v[4 * j] = fmaf(c.x, y[r], v[4 * j]);
-        v[4 * j + 1] = fmaf(c.y, y[r], v[4 * j + 1]);
-        v[4 * j + 2] = fmaf(c.z, y[r], v[4 * j + 2]);
-        v[4 * j + 3] = fmaf(c.w, y[r], v[4 * j + 3]);
+        T q[4];
+        q_quad(P, tf, i + r, g, q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[4 * g + e] = vfma(q[e], y[r], v[4 * g + e]);
       }
     }
   }
 }
 
-template <int N, class Dst>
-__device__ __forceinline__ void post_fwd(const float (&v)[N], const TfDev& tf,
-                                         const float* __restrict__ P, const Dst& dst) {
-  const float* Q = P + tf.q_off;
+template <int N, class T, class Dst>
+__device__ __forceinline__ void post_fwd(const T (&v)[N], const TfDev& tf, const float* __restrict__ P,
+                                         const Dst& dst) {
   switch (tf.kt) {
-    case 4: post_fwd_k<N, 4>(v, Q, dst); break;
-    case 8: if constexpr (N >= 8) { post_fwd_k<N, 8>(v, Q, dst); } break;
-    case 16: if constexpr (N >= 16) { post_fwd_k<N, 16>(v, Q, dst); } break;
-    case 32: if constexpr (N >= 32) { post_fwd_k<N, 32>(v, Q, dst); } break;
-    default: if constexpr (N >= 64) { post_fwd_k<N, 64>(v, Q, dst); } break;
+    case 4: post_fwd_k<N, 4>(v, tf, P, dst); break;
+    case 8: if constexpr (N >= 8) { post_fwd_k<N, 8>(v, tf, P, dst); } break;
+    case 16: if constexpr (N >= 16) { post_fwd_k<N, 16>(v, tf, P, dst); } break;
+    case 32: if constexpr (N >= 32) { post_fwd_k<N, 32>(v, tf, P, dst); } break;
+    default: if constexpr (N >= 64) { post_fwd_k<N, 64>(v, tf, P, dst); } break;
   }
 }
 
-template <int N, class Src>
-__device__ __forceinline__ void post_inv(float (&v)[N], const TfDev& tf, const float* __restrict__ P,
-                                         const Src& src) {
-  const float* Q = P + tf.q_off;
+template <int N, class T, class Src>
+__device__ __forceinline__ void post_inv(T (&v)[N], const TfDev& tf, const float* __restrict__ P, const Src& src) {
   switch (tf.kt) {
-    case 4: post_inv_k<N, 4>(v, Q, src); break;
-    case 8: if constexpr (N >= 8) { post_inv_k<N, 8>(v, Q, src); } break;
-    case 16: if constexpr (N >= 16) { post_inv_k<N, 16>(v, Q, src); } break;
-    case 32: if constexpr (N >= 32) { post_inv_k<N, 32>(v, Q, src); } break;
-    default: if constexpr (N >= 64) { post_inv_k<N, 64>(v, Q, src); } break;
+    case 4: post_inv_k<N, 4>(v, tf, P, src); break;
+    case 8: if constexpr (N >= 8) { post_inv_k<N, 8>(v, tf, P, src); } break;
+    case 16: if constexpr (N >= 16) { post_inv_k<N, 16>(v, tf, P, src); } break;
+    case 32: if constexpr (N >= 32) { post_inv_k<N, 32>(v, tf, P, src); } break;
+    default: if constexpr (N >= 64) { post_inv_k<N, 64>(v, tf, P, src); } break;
   }
 }
 
@@ -257,10 +284,10 @@ struct DstGCol {
 // ---------------------------------------------------------------------------------
 // One line of a pass.  Forward: A (band), B (core), C (post).  Inverse: C^T, B^T, A^T.
 // ---------------------------------------------------------------------------------
-template <int N, bool INV, bool I16, class Src, class Dst>
+template <int N, bool INV, bool I16, class T = float, class Src, class Dst>
 __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __restrict__ P,
                                                const Src& src, const Dst& dst) {
-  float v[N];
+  T v[N];
   if constexpr (I16) {
     src.template load_i16<N>(v);
   } else {
@@ -281,6 +308,48 @@ __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __r
     dst.template store<N>(v);
   }
 }
+
+// Two lines seen as one line of float2 elements (line a in .x, line b in .y).
+template <class A>
+struct Pair {
+  A a, b;
+  template <int N>
+  __device__ __forceinline__ void load(float2 (&v)[N]) const {
+    float x[N], y[N];
+    a.template load<N>(x);
+    b.template load<N>(y);
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = make_float2(x[i], y[i]);
+  }
+  template <int N>
+  __device__ __forceinline__ void load_i16(float2 (&v)[N]) const {
+    float x[N], y[N];
+    a.template load_i16<N>(x);
+    b.template load_i16<N>(y);
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = make_float2(x[i], y[i]);
+  }
+  __device__ __forceinline__ float2 get_rt(int i) const { return make_float2(a.get_rt(i), b.get_rt(i)); }
+  __device__ __forceinline__ void put(int i, float2 x) const {
+    a.put(i, x.x);
+    b.put(i, x.y);
+  }
+  __device__ __forceinline__ void put_rt(int i, float2 x) const {
+    a.put_rt(i, x.x);
+    b.put_rt(i, x.y);
+  }
+  template <int N>
+  __device__ __forceinline__ void store(const float2 (&v)[N]) const {
+    float x[N], y[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      x[i] = v[i].x;
+      y[i] = v[i].y;
+    }
+    a.template store<N>(x);
+    b.template store<N>(y);
+  }
+};
 
 // ---------------------------------------------------------------------------------
 // Asynchronous 16-B global -> shared copies (staging of the input tile).

@@ -1,4 +1,5 @@
-// Fused, persistent 2-D adjusted-transform kernels (forward and inverse).
+// Fused, persistent 2-D adjusted-transform kernels (forward and inverse); the two
+// directions are instantiated in adjtx_fused_fwd.cu and adjtx_fused_inv.cu.
 //
 // One CTA processes one tile at a time: a group of blocks that share
 // (w, h, tf_h, tf_v), at most 4096 coefficients.  Per tile:
@@ -16,6 +17,8 @@
 // scheduling state, so a launch needs no separate reset.  No CTA ever waits for another.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#pragma once
 
 #include "adjtx_device.cuh"
 #include "adjtx_kernels.h"
@@ -62,14 +65,26 @@ __device__ __forceinline__ void stage_tile(const TileDev& td, const uint32_t* sO
   }
 }
 
+// Lines of at most 32 samples are transformed two at a time (lines l and l + half share a
+// thread, packed FP32x2 arithmetic); 64-sample lines one per thread.
 template <int W, bool INV, int THREADS>
 __device__ __forceinline__ void row_pass(const TfDev& tf, const float* __restrict__ P, float* buf, int nb, int h) {
   constexpr int SH = sw_shift(W), MK = sw_mask(W);
   const int nlines = nb * h;
-  for (int l = threadIdx.x; l < nlines; l += THREADS) {
-    const int r = l & (h - 1);
-    RowSw row{buf + l * W, (r >> SH) & MK};
-    line_transform<W, INV, !INV>(tf, P, row, row);
+  if constexpr (W <= 32) {
+    const int half = nlines >> 1;  // nb * h is even (h >= 4)
+    for (int l = threadIdx.x; l < half; l += THREADS) {
+      const int l2 = l + half;
+      Pair<RowSw> row{RowSw{buf + l * W, ((l & (h - 1)) >> SH) & MK},
+                      RowSw{buf + l2 * W, ((l2 & (h - 1)) >> SH) & MK}};
+      line_transform<W, INV, !INV, float2>(tf, P, row, row);
+    }
+  } else {
+    for (int l = threadIdx.x; l < nlines; l += THREADS) {
+      const int r = l & (h - 1);
+      RowSw row{buf + l * W, (r >> SH) & MK};
+      line_transform<W, INV, !INV>(tf, P, row, row);
+    }
   }
 }
 
@@ -78,11 +93,22 @@ __device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restric
                                          const uint32_t* sOff, float* __restrict__ out, int nb) {
   constexpr int lgw = ilog2(W);
   const int nlines = nb * W;
-  for (int l = threadIdx.x; l < nlines; l += THREADS) {
-    const int b = l >> lgw, c = l & (W - 1);
-    ColSw<W> src(buf + b * (W * H), c);
-    DstGCol<W> dst{out + (size_t)sOff[b] * 16 + c};
-    line_transform<H, INV, false>(tf, P, src, dst);
+  if constexpr (H <= 32) {
+    const int half = nlines >> 1;
+    for (int l = threadIdx.x; l < half; l += THREADS) {
+      const int l2 = l + half;
+      const int b1 = l >> lgw, c1 = l & (W - 1), b2 = l2 >> lgw, c2 = l2 & (W - 1);
+      Pair<ColSw<W>> src{ColSw<W>(buf + b1 * (W * H), c1), ColSw<W>(buf + b2 * (W * H), c2)};
+      Pair<DstGCol<W>> dst{DstGCol<W>{out + (size_t)sOff[b1] * 16 + c1}, DstGCol<W>{out + (size_t)sOff[b2] * 16 + c2}};
+      line_transform<H, INV, false, float2>(tf, P, src, dst);
+    }
+  } else {
+    for (int l = threadIdx.x; l < nlines; l += THREADS) {
+      const int b = l >> lgw, c = l & (W - 1);
+      ColSw<W> src(buf + b * (W * H), c);
+      DstGCol<W> dst{out + (size_t)sOff[b] * 16 + c};
+      line_transform<H, INV, false>(tf, P, src, dst);
+    }
   }
 }
 
@@ -222,27 +248,6 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
     if (tid == 0) a.sched->done = 0u;
     __threadfence();
   }
-}
-
-template <bool INV>
-static const void* fused_fn(int threads) {
-  switch (threads) {
-    case 64: return reinterpret_cast<const void*>(&fused_kernel<INV, 64>);
-    case 128: return reinterpret_cast<const void*>(&fused_kernel<INV, 128>);
-    default: return nullptr;
-  }
-}
-
-const void* fused_kernel_ptr(bool inverse, int threads) {
-  return inverse ? fused_fn<true>(threads) : fused_fn<false>(threads);
-}
-
-cudaError_t launch_fused(bool inverse, int threads, int grid, const FusedArgs& args, cudaStream_t stream) {
-  const void* fn = fused_kernel_ptr(inverse, threads);
-  if (!fn) return cudaErrorInvalidValue;
-  FusedArgs a = args;
-  void* params[] = {&a};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, kSmemBytes, stream);
 }
 
 }  // namespace adjtx

@@ -54,6 +54,8 @@ cudaError_t launch_bwd(bool i16, int grid, const BwdArgs& args, double* M, const
                        const int* m_off, const int* g_off, const int* kq, float* gparams, cudaStream_t stream);
 
 const void* fused_kernel_ptr(bool inverse, int threads);
+const void* fused_fwd_ptr();
+const void* fused_inv_ptr();
 void set_last_error(const char* msg);
 cudaError_t launch_fused(bool inverse, int threads, int grid, const FusedArgs& args, cudaStream_t stream);
 

@@ -202,6 +202,8 @@ def f32(x):
 
 
 def emit(N, core, prog):
+    """Straight-line code of one core, templated on the element type T (float, or float2 for
+    two lines at once); arithmetic goes through the helpers of vec_ops.cuh."""
     ins, ops, outs = prog
     lines = []
     cur = {}
@@ -213,26 +215,26 @@ def emit(N, core, prog):
         tmp[0] += 1
         return f"t{tmp[0]}"
 
-    def lin(terms):
-        parts = []
-        for coef, (name, sign) in terms:
-            cf = coef * sign
-            if cf == 0.0:
-                continue
-            if cf == 1.0:
-                parts.append(("+", name))
-            elif cf == -1.0:
-                parts.append(("-", name))
-            elif cf > 0:
-                parts.append(("+", f"{f32(cf)} * {name}"))
-            else:
-                parts.append(("-", f"{f32(-cf)} * {name}"))
-        if not parts:
-            return "0.0f"
-        s = ("-" if parts[0][0] == "-" else "") + parts[0][1]
-        for sg, t in parts[1:]:
-            s += f" {sg} {t}"
-        return s
+    def comb(terms):
+        """Expression for sum(coef * sign * name) over two terms."""
+        ts = [(coef * sign, name) for coef, (name, sign) in terms if coef * sign != 0.0]
+        if not ts:
+            return "vzero(v[0])"
+        if len(ts) == 1:
+            c, a = ts[0]
+            if c == 1.0:
+                return a
+            if c == -1.0:
+                return f"vneg({a})"
+            return f"vmul({f32(c)}, {a})"
+        (c1, a), (c2, b) = ts
+        if c1 == 1.0 and c2 == 1.0:
+            return f"vadd({a}, {b})"
+        if c1 == 1.0 and c2 == -1.0:
+            return f"vsub({a}, {b})"
+        if c1 == -1.0 and c2 == 1.0:
+            return f"vsub({b}, {a})"
+        return f"vmac({f32(c1)}, {a}, {f32(c2)}, {b})"
 
     n_add = n_mat = 0
     for op in ops:
@@ -240,18 +242,20 @@ def emit(N, core, prog):
             _, i, j = op
             (a, sa), (b, sb) = cur[i], cur[j]
             ts, td = new(), new()
-            rel = "+" if sa * sb > 0 else "-"
-            inv = "-" if sa * sb > 0 else "+"
-            lines.append(f"  const float {ts} = {a} {rel} {b};")
-            lines.append(f"  const float {td} = {a} {inv} {b};")
+            if sa * sb > 0:
+                lines.append(f"    const T {ts} = vadd({a}, {b});")
+                lines.append(f"    const T {td} = vsub({a}, {b});")
+            else:
+                lines.append(f"    const T {ts} = vsub({a}, {b});")
+                lines.append(f"    const T {td} = vadd({a}, {b});")
             cur[i], cur[j] = (ts, sa), (td, sa)
             n_add += 1
         elif op[0] == "mat":
             _, i, j, a, b, c, d = op
             x, y = cur[i], cur[j]
             ti, tj = new(), new()
-            lines.append(f"  const float {ti} = {lin([(a, x), (b, y)])};")
-            lines.append(f"  const float {tj} = {lin([(c, x), (d, y)])};")
+            lines.append(f"    const T {ti} = {comb([(a, x), (b, y)])};")
+            lines.append(f"    const T {tj} = {comb([(c, x), (d, y)])};")
             cur[i], cur[j] = (ti, 1), (tj, 1)
             n_mat += 1
         else:
@@ -259,13 +263,14 @@ def emit(N, core, prog):
             cur[op[1]] = (name, -sign)
     for k in range(N):
         name, sign = cur[outs[k]]
-        lines.append(f"  v[{k}] = {'-' if sign < 0 else ''}{name};")
+        lines.append(f"    v[{k}] = {'vneg(' + name + ')' if sign < 0 else name};")
     head = (f"// {CORE_NAMES[core]} N={N}: {n_add} butterflies (2 FADD), {n_mat} rotations "
             f"(2 FMUL + 2 FFMA) = {2 * n_add + 4 * n_mat} FP32 ops, "
             f"{(2 * n_add + 4 * n_mat) / N:.2f} per sample")
     body = "\n".join(lines)
     return (f"{head}\ntemplate <> struct Core<{N}, {core}> {{\n"
-            f"  static __device__ __forceinline__ void apply(float (&v)[{N}]) {{\n{body}\n  }}\n}};\n")
+            f"  template <class T>\n"
+            f"  static __device__ __forceinline__ void apply(T (&v)[{N}]) {{\n{body}\n  }}\n}};\n")
 
 
 def generate() -> str:
@@ -273,6 +278,7 @@ def generate() -> str:
         "// Generated by gen_cores.py: fast orthonormal DCT-2 / DCT-3 / DST-2 / DST-3 cores.\n"
         "// Do not edit; regenerate with `python gen_cores.py`.\n"
         "#pragma once\n\n"
+        "#include \"vec_ops.cuh\"\n\n"
         "template <int N, int CORE> struct Core;\n\n"
     ]
     for N in SIZES:
