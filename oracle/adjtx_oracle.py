@@ -446,3 +446,145 @@ def proxy_loss(Y):
 
 __all__ += ["grad_2d", "grad_band_angles", "grad_post_q", "skew_from_params", "cayley",
             "cayley_grad", "basis_loss", "proxy_loss"]
+
+
+# --------------------------------------------------------------------------
+# Simultaneous DST-7 and DCT-8 adjustments for the encoder search (Section 2.3).
+#
+# With a top-left post-adjustment after the DCT-2, S T^(C2) = T^(C2) R turns Eq. 3 into
+# Eq. 5: the DCT-8 adjustment is C^(C8) = S C^(S7) S.  An encoder that tries the 2-D
+# DCT-2 and every (vertical, horizontal) pairing of DST-7 and DCT-8 therefore needs one
+# DCT-2 per line plus the K x K products of the first K outputs; every other coefficient
+# of the four adjusted transforms equals the DCT-2 one.
+# --------------------------------------------------------------------------
+
+# (vertical, horizontal) pairings in output order; "S" = DST-7 adjustment, "C" = DCT-8.
+MULTI_COMBOS = ("SS", "SC", "CS", "CC")
+
+
+def post_c8_from_s7(Q) -> np.ndarray:
+    """K x K block of C^(C8) = S C^(S7) S (Eq. 5): Q with entry (i, j) times (-1)^(i+j)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    S = alt_sign(Q.shape[0])
+    return S @ Q @ S
+
+
+def multiple_1d(N: int, Q=None):
+    """(T^(C2), C^(S7) T^(C2), C^(C8) T^(C2)) for C^(S7) = diag(Q, I); Q None means K = 0
+    (no adjustment: all three are the DCT-2).  C^(C8) is formed as S C^(S7) S with the N x N
+    sign matrix, exactly as Eq. 5 states it."""
+    B = dct2(N)
+    if Q is None or np.asarray(Q).size == 0:
+        return B, B.copy(), B.copy()
+    C = post_matrix(N, Q)
+    S = alt_sign(N)
+    return B, C @ B, S @ C @ S @ B
+
+
+def multiple_2d(X, Qh=None, Qv=None) -> dict:
+    """Y_DD = T_v X T_h^T (2-D DCT-2) and Y_ab = H_a^v X (H_b^h)^T for every pairing ab of
+    MULTI_COMBOS (a vertical, b horizontal), each by its own dense product."""
+    X = np.asarray(X, dtype=np.float64)
+    h, w = X.shape[-2:]
+    Dh, Sh, Ch = multiple_1d(w, Qh)
+    Dv, Sv, Cv = multiple_1d(h, Qv)
+    hor = {"S": Sh, "C": Ch}
+    ver = {"S": Sv, "C": Cv}
+    out = {"DD": forward_2d(X, Dh, Dv)}
+    for ab in MULTI_COMBOS:
+        out[ab] = forward_2d(X, hor[ab[1]], ver[ab[0]])
+    return out
+
+
+def multiple_side_size(w: int, h: int, kh: int, kv: int) -> int:
+    """Floats of one block's distinct adjusted coefficients (layout of ``multiple_side``):
+    2 kv (w - kh) + 2 (h - kv) kh + 4 kv kh."""
+    return 2 * kv * (w - kh) + 2 * (h - kv) * kh + 4 * kv * kh
+
+
+def multiple_side(Y: dict, kh: int, kv: int) -> np.ndarray:
+    """The coefficients of the four adjusted pairings that can differ from Y_DD, each
+    distinct value once, concatenated (each region row-major):
+      R_S, R_C            rows < kv, columns >= kh of Y_S*, Y_C* (independent of the
+                          horizontal choice there);
+      L_S, L_C            rows >= kv, columns < kh of Y_*S, Y_*C (independent of the
+                          vertical choice);
+      X_SS, X_SC, X_CS, X_CC   rows < kv, columns < kh of each pairing.
+    Everywhere else every pairing equals Y_DD."""
+    parts = [Y["SS"][:kv, kh:], Y["CS"][:kv, kh:], Y["SS"][kv:, :kh], Y["SC"][kv:, :kh]]
+    parts += [Y[ab][:kv, :kh] for ab in MULTI_COMBOS]
+    return np.concatenate([np.asarray(p).ravel() for p in parts])
+
+
+def multiple_assemble(y_dd, side, w: int, h: int, kh: int, kv: int) -> dict:
+    """Inverse of the layout: the full h x w block of every pairing from Y_DD and the
+    block's side regions."""
+    y_dd = np.asarray(y_dd, dtype=np.float64).reshape(h, w)
+    side = np.asarray(side, dtype=np.float64)
+    pos = 0
+
+    def take(r, c):
+        nonlocal pos
+        v = side[pos:pos + r * c].reshape(r, c)
+        pos += r * c
+        return v
+
+    R = {"S": take(kv, w - kh), "C": take(kv, w - kh)}
+    L = {"S": take(h - kv, kh), "C": take(h - kv, kh)}
+    out = {"DD": y_dd.copy()}
+    for ab in MULTI_COMBOS:
+        Y = y_dd.copy()
+        Y[:kv, kh:] = R[ab[0]]
+        Y[kv:, :kh] = L[ab[1]]
+        Y[:kv, :kh] = take(kv, kh)
+        out[ab] = Y
+    return out
+
+
+def multiple_blocks(x_flat, blocks, tfs):
+    """FP64 "Multiple" forward of a packed block buffer: (Y_DD in the blocks' layout,
+    the side buffer, side offsets).  Every transform a block uses must be a DCT-2 with no
+    adjustment (K = 0) or a post-adjustment with K <= n/2.  Block i's side regions start at
+    offsets[i] (floats; blocks in list order, each region rounded up to a multiple of 4);
+    offsets[-1] is the total."""
+    x_flat = np.asarray(x_flat)
+    y = np.zeros(x_flat.shape[0], dtype=np.float64)
+
+    def kq(t):
+        kind = int(t.kind if not isinstance(t, dict) else t["kind"])
+        if kind == KIND_NONE:
+            return 0, None
+        q = np.asarray(t.q if not isinstance(t, dict) else t["q"], dtype=np.float64)
+        return q.shape[0], q
+
+    for t in tfs:
+        get = (lambda k: t[k]) if isinstance(t, dict) else (lambda k: getattr(t, k))
+        kind = int(get("kind"))
+        if int(get("core")) != 0 or kind not in (KIND_NONE, KIND_POST):
+            raise ValueError("the Multiple forward needs DCT-2 cores with no adjustment or a post-adjustment")
+        if kind == KIND_POST and 2 * np.asarray(get("q")).shape[0] > int(get("n")):
+            raise ValueError("the Multiple forward needs K <= n/2")
+
+    sizes = []
+    for b in blocks:
+        w, h = int(b["w"]), int(b["h"])
+        kh, _ = kq(tfs[int(b["tf_h"])])
+        kv, _ = kq(tfs[int(b["tf_v"])])
+        s = multiple_side_size(w, h, kh, kv)
+        sizes.append((s + 3) // 4 * 4)
+    offsets = np.concatenate([[0], np.cumsum(np.asarray(sizes, dtype=np.int64))]).astype(np.int64)
+    side = np.zeros(int(offsets[-1]), dtype=np.float64)
+    for i, b in enumerate(blocks):
+        w, h, o = int(b["w"]), int(b["h"]), int(b["offset"])
+        kh, qh = kq(tfs[int(b["tf_h"])])
+        kv, qv = kq(tfs[int(b["tf_v"])])
+        X = x_flat[o:o + w * h].astype(np.float64).reshape(h, w)
+        Y = multiple_2d(X, qh, qv)
+        y[o:o + w * h] = Y["DD"].ravel()
+        s = multiple_side(Y, kh, kv)
+        side[offsets[i]:offsets[i] + s.size] = s
+    return y, side, offsets
+
+
+__all__ += ["MULTI_COMBOS", "post_c8_from_s7", "multiple_1d", "multiple_2d", "multiple_side_size",
+            "multiple_side", "multiple_assemble", "multiple_blocks"]
