@@ -10,8 +10,10 @@ kernels are timed with CUDA events on their stream.
 
 Extra fields: `e2e` (the same metric through the host-buffer C-ABI entry points,
 copies included), `roofline` (HBM roofline of the dominant kernel from
-algorithmic bytes), `cpu_baseline` (the FP64 oracle on the host cores) and the
-SM clocks sampled during the timed region.
+algorithmic bytes), `cpu_baseline` (the FP64 oracle on the host cores), the
+SM clocks sampled during the timed region, and `multiple`: the encoder's
+simultaneous DST-7 / DCT-8 forward (Section 2.3) on the same frame tiling against
+five separate forwards.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -44,6 +46,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--frames", type=int, default=8, help="frames of the workload (profiling uses fewer)")
+    p.add_argument("--no-multiple", action="store_true", help="skip the Multiple-forward measurement")
     return p.parse_args()
 
 
@@ -220,6 +223,67 @@ def run_reference(args):
     return 0
 
 
+def bench_multiple(args, rank, dev, stream, flush, peak):
+    """The encoder's DST-7 / DCT-8 search (Section 2.3) on the same frame tiling: one
+    Multiple forward (2-D DCT-2 + the distinct coefficients of the four adjusted pairings)
+    against five separate fused forwards (DCT-2 and each pairing with its own post
+    transforms, Q or S Q S), every launch after an L2 flush, median of the timed repeats."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    import paper_2505_23618_gb300 as adj
+
+    wl = synth.config3_multiple(seed=3 + 1000 * rank, frames=args.frames)
+    coefs, nb = wl.total, int(wl.blocks.size)
+    reps = max(3, min(args.steps, 30))
+    x = torch.from_numpy(wl.data).to(dev)
+    y = torch.empty(coefs, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps)]
+        for e in ev:
+            flush.fill_(5.0)
+            e[0].record(stream)
+            fn()
+            e[1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+
+    with adj.Plan(wl.tfs) as plan:
+        plan.set_blocks(wl.blocks, coefs)
+        off = plan.prepare_multiple()
+        side = torch.empty(int(off[-1]), dtype=torch.float32, device=dev)
+        ms_multi = timed(lambda: plan.fwd_multiple(x, y, side, stream))
+        n_tiles = plan.info()["n_tiles"]
+    # the five transforms one by one: DCT-2, then (vertical, horizontal) = SS, SC, CS, CC
+    n_dir = len(synth.SIZES)
+    ms_sep = 0.0
+    for combo in ("DD",) + tuple(oracle.MULTI_COMBOS):
+        tfs = []
+        for d, t in enumerate(wl.tfs):
+            c = combo[1] if d < n_dir else combo[0]     # first half horizontal, second vertical
+            if c == "D":
+                tfs.append(synth.Tf(n=t.n, core=0))
+            else:
+                q = t.q if c == "S" else oracle.post_c8_from_s7(t.q)
+                tfs.append(synth.Tf(n=t.n, core=0, kind=synth.KIND_POST, q=q))
+        with adj.Plan(tfs) as p5:
+            p5.set_blocks(wl.blocks, coefs)
+            ms_sep += timed(lambda: p5.fwd(x, y, stream))
+    algo = coefs * 6 + int(off[-1]) * 4 + n_tiles * 16 + nb * 8
+    gbs = algo / (ms_multi * 1e-3) / 1e9
+    return {"workload": wl.name, "value": round(coefs / (ms_multi * 1e-3) / 1e9, 3), "unit": UNIT,
+            "ms": round(ms_multi, 4), "side_floats": int(off[-1]),
+            "algorithmic_bytes": algo, "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+            "five_separate_ms": round(ms_sep, 4), "vs_five_separate": round(ms_sep / ms_multi, 3),
+            "how": "one launch for DCT-2 + 4 DST-7/DCT-8 pairings vs 5 fused forwards, median of "
+                   f"{reps} L2-flushed repeats"}
+
+
 def run_fused(args):
     import numpy as np
     import torch
@@ -311,6 +375,9 @@ def run_fused(args):
     g_inv.close()
     del yp, xrp
 
+    peak, peak_src = measured_peak()
+    multiple = bench_multiple(args, rank, dev, stream, flush, peak) if not args.no_multiple else None
+
     # end to end through the host-buffer C-ABI calls (pinned memory), copies included
     h_x = torch.from_numpy(wl.data).pin_memory()
     h_y = torch.empty(coefs, dtype=torch.float32).pin_memory()
@@ -331,7 +398,6 @@ def run_fused(args):
         "fwd": {"bytes": coefs * 6 + meta, "ms": float(t_fwd.mean() * 1e3)},
         "inv": {"bytes": coefs * 8 + meta, "ms": float(t_inv.mean() * 1e3)},
     }
-    peak, peak_src = measured_peak()
     for k in kern.values():
         k["gbs"] = k["bytes"] / (k["ms"] * 1e-3) / 1e9
         k["frac"] = k["gbs"] / peak
@@ -360,6 +426,7 @@ def run_fused(args):
                       "timed_steps": plain_steps, "how": "CUDA-graph replay of one launch per block size and step",
                       "roundtrip_max_abs_err": plain_rt},
             "roofline": roof,
+            "multiple": multiple,
             "kernels": {k: {"ms": round(v["ms"], 4), "GB/s": round(v["gbs"], 1), "frac": round(v["frac"], 4)}
                         for k, v in kern.items()},
             "clocks": clk.summary(),

@@ -146,6 +146,43 @@ int adj_transform_fwd(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, v
 int adj_transform_inv(adj_plan_t* plan, const float* d_coef, float* d_resid_out, void* stream);
 
 /*
+ * Simultaneous DST-7 / DCT-8 adjustments for an encoder's transform search ("Multiple",
+ * Section 2.3).  With a post-adjustment after the DCT-2, S T^(C2) = T^(C2) R turns the
+ * DCT-8 flip of Eq. 3 into Eq. 5: if C^(S7) = diag(Q, I) adjusts the DCT-2 towards the
+ * DST-7, then C^(C8) = S C^(S7) S adjusts it towards the DCT-8 (Q with its signs flipped in
+ * a chessboard pattern).  The encoder wants, per block, the 2-D DCT-2 and the four
+ * (vertical a, horizontal b) pairings of the two adjusted transforms,
+ *   Y_DD = T_v X T_h^T,   Y_ab = H_a,v X H_b,h^T   (a, b in {S = DST-7, C = DCT-8}),
+ * and only the first K lines of an adjusted transform differ from the DCT-2, so each
+ * distinct coefficient is computed and stored once: Y_DD in place, plus per block these
+ * side regions (kh, kv = the K of the horizontal / vertical transform, 0 when it has no
+ * adjustment; a, b = 0 for DST-7, 1 for DCT-8; each region row-major, in this order):
+ *   R_0, R_1           rows < kv, columns >= kh of the pairings with vertical a: kv x (w - kh)
+ *   L_0, L_1           rows >= kv, columns < kh of the pairings with horizontal b: (h - kv) x kh
+ *   X_00, X_01, X_10, X_11   rows < kv, columns < kh of pairing (a, b): kv x kh
+ * that is 2 kv w + 2 h kh floats, rounded up to a multiple of 4.  Every other coefficient
+ * of Y_ab equals Y_DD.  The even/odd split of Q gives both adjustments of a line for the
+ * multiplications of one K x K product.
+ *
+ * adj_plan_prepare_multiple validates the current block list for this form: every
+ * transform a block uses must have core ADJ_CORE_DCT2 and kind ADJ_ADJ_NONE or
+ * ADJ_ADJ_POST_BLOCK with 2K <= n (INVALID_ARG / UNSUPPORTED_SIZE otherwise; the q of the
+ * transform is Q of C^(S7)).  Side regions follow the order of the block list given to
+ * adj_plan_set_blocks: block i starts at side_offsets[i] floats (host array of n_blocks + 1
+ * entries, optional; the last entry is the total), *side_total = total floats (optional).
+ * Call it again after adj_plan_set_blocks; adj_plan_set_tuning and adj_plan_autotune keep it.
+ *
+ * adj_transform_fwd_multiple: d_resid (int16, device) -> d_coef (FP32, device, Y_DD in the
+ * layout of adj_transform_fwd) and d_side (FP32, device, side_total floats; may be NULL
+ * when side_total is 0); all 16-B aligned.  One persistent kernel launch, asynchronous
+ * on `stream`.  Errors: INVALID_ARG (also: not prepared), NO_BLOCKS, MISALIGNED, CUDA.
+ * The inverse of a chosen pairing is adj_transform_inv with post transforms Q or S Q S.
+ */
+int adj_plan_prepare_multiple(adj_plan_t* plan, int64_t* side_offsets, int64_t* side_total);
+int adj_transform_fwd_multiple(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, float* d_side,
+                               void* stream);
+
+/*
  * Backward of adj_transform_fwd for fitting the adjustments (the paper designs them by a
  * constrained least-squares fit, Eq. 2, through the Givens factorisation after it).
  * Given the forward input d_x (int16 or FP32 per x_dtype, device, the same layout) and
@@ -232,12 +269,14 @@ int adj_transform_fwd_uniform_noalloc(const adj_1d_desc_t* tf_h, const adj_1d_de
  *   ADJ_GRAPH_FWD_PLAIN / ADJ_GRAPH_INV_PLAIN  the plain form (d_in -> d_out)
  *   ADJ_GRAPH_ROUNDTRIP                        fused forward d_in -> d_out, then fused
  *                                              inverse d_out -> d_out2
+ *   ADJ_GRAPH_FWD_MULTIPLE                     Multiple forward d_in -> d_out (Y_DD) and
+ *                                              d_out2 (side regions)
  * The graph refers to the plan's tables: replace neither the block list nor the plan while
  * it exists (adj_plan_update_params is fine).  Errors: INVALID_ARG, NO_BLOCKS, MISALIGNED, CUDA.
  */
 typedef struct adj_graph adj_graph_t;
 enum { ADJ_GRAPH_FWD = 0, ADJ_GRAPH_INV = 1, ADJ_GRAPH_FWD_PLAIN = 2, ADJ_GRAPH_INV_PLAIN = 3,
-       ADJ_GRAPH_ROUNDTRIP = 4 };
+       ADJ_GRAPH_ROUNDTRIP = 4, ADJ_GRAPH_FWD_MULTIPLE = 5 };
 int adj_graph_create(adj_plan_t* plan, int32_t what, const void* d_in, float* d_out, float* d_out2,
                      adj_graph_t** graph);
 int adj_graph_launch(adj_graph_t* graph, void* stream);

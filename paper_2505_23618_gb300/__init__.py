@@ -8,7 +8,7 @@ library behind the C ABI of include/adjtx.h; this package only marshals argument
 
 from ._lib import (ADJ_OK, BLOCK_DTYPE, ERR_CODE, ERRORS, EXPORTED, LIB_PATH, AdjError,  # noqa: F401
                    Plan, check, lib, load)
-from .torch_api import forward, inverse, roundtrip  # noqa: F401
+from .torch_api import forward, forward_multiple, inverse, roundtrip  # noqa: F401
 
-__all__ = ["Plan", "AdjError", "forward", "inverse", "roundtrip", "BLOCK_DTYPE", "lib",
+__all__ = ["Plan", "AdjError", "forward", "forward_multiple", "inverse", "roundtrip", "BLOCK_DTYPE", "lib",
            "LIB_PATH", "EXPORTED"]

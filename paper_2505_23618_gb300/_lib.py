@@ -32,10 +32,10 @@ EXPORTED = (
     "adj_transform_fwd_uniform_noalloc", "adj_transform_fwd_plain", "adj_transform_inv_plain",
     "adj_graph_create", "adj_graph_launch", "adj_graph_destroy", "adj_transform_bwd",
     "adj_plan_param_layout", "adj_coding_gain_proxy", "adj_plan_get_tuning", "adj_plan_set_tuning",
-    "adj_plan_autotune",
+    "adj_plan_autotune", "adj_plan_prepare_multiple", "adj_transform_fwd_multiple",
 )
 DTYPE_INT16, DTYPE_FP32 = 0, 1
-GRAPH_FWD, GRAPH_INV, GRAPH_FWD_PLAIN, GRAPH_INV_PLAIN, GRAPH_ROUNDTRIP = range(5)
+GRAPH_FWD, GRAPH_INV, GRAPH_FWD_PLAIN, GRAPH_INV_PLAIN, GRAPH_ROUNDTRIP, GRAPH_FWD_MULTIPLE = range(6)
 
 
 class Adj1dDesc(C.Structure):
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.adj_plan_get_tuning.argtypes = [vp, C.POINTER(AdjTuning)]
     lib.adj_plan_set_tuning.argtypes = [vp, C.POINTER(AdjTuning)]
     lib.adj_plan_autotune.argtypes = [vp, vp, vp, vp, C.c_char_p, i32, vp]
+    lib.adj_plan_prepare_multiple.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.adj_transform_fwd_multiple.argtypes = [vp, vp, vp, vp, vp]
     lib.adj_graph_create.argtypes = [vp, i32, vp, vp, vp, C.POINTER(vp)]
     lib.adj_graph_launch.argtypes = [vp, vp]
     lib.adj_graph_destroy.argtypes = [vp]
@@ -175,12 +177,14 @@ class Plan:
         d = _DescArray(self.tfs)
         check(self._lib.adj_plan_create(C.byref(self._h), d.arr, d.n, flags))
         self.total = 0
+        self.n_blocks = 0
 
     def set_blocks(self, blocks: np.ndarray, total: int):
         b = np.ascontiguousarray(blocks).view(BLOCK_DTYPE)
         check(self._lib.adj_plan_set_blocks(self._h, b.ctypes.data if b.size else None,
                                             b.size, int(total)))
         self.total = int(total)
+        self.n_blocks = int(b.size)
         return self
 
     def update_params(self, tfs):
@@ -193,6 +197,21 @@ class Plan:
 
     def inv(self, d_in, d_out, stream=None):
         check(self._lib.adj_transform_inv(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+    def prepare_multiple(self):
+        """Validate the block list for the Multiple forward; returns the side offsets in
+        floats (n_blocks + 1 entries, block list order; the last is the total)."""
+        off = np.zeros(self.n_blocks + 1, dtype=np.int64)
+        total = C.c_int64()
+        check(self._lib.adj_plan_prepare_multiple(self._h, off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                                  C.byref(total)))
+        return off
+
+    def fwd_multiple(self, d_in, d_coef, d_side, stream=None):
+        """2-D DCT-2 into d_coef and the distinct DST-7 / DCT-8 adjusted coefficients of the
+        four pairings into d_side (see adj_transform_fwd_multiple)."""
+        check(self._lib.adj_transform_fwd_multiple(self._h, _ptr(d_in), _ptr(d_coef), _ptr(d_side),
+                                                   _stream(stream)))
 
     def fwd_plain(self, d_in, d_out, stream=None):
         check(self._lib.adj_transform_fwd_plain(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))

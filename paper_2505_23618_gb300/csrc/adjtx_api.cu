@@ -67,7 +67,7 @@ struct adj_plan {
   TileDev* d_tiles = nullptr;
   uint32_t* d_tile_blk = nullptr;
   int n_tiles = 0;
-  SchedState* d_sched = nullptr;  // [0] forward, [1] inverse
+  SchedState* d_sched = nullptr;  // [0] forward, [1] inverse, [2] Multiple forward
   unsigned* d_range_begin = nullptr;
   int n_ranges = 0;
   int grid_fwd = 0, grid_inv = 0;
@@ -84,6 +84,12 @@ struct adj_plan {
   double* d_M = nullptr;
   int bwd_grid = 0;
   std::vector<adj_block_t> blocks;     // validated, in storage order
+  std::vector<int64_t> orig;           // caller's index of each entry of `blocks`
+  // Multiple forward: prepared block list, side offsets in the caller's block order
+  bool multi = false;
+  std::vector<int64_t> side_off;
+  uint32_t* d_tile_side = nullptr;     // side offset / 4, parallel to d_tile_blk
+  int occ_multi = 0, grid_multi = 0;
   adj_tuning_t tuning{};
   int occ_fwd = 0, occ_inv = 0;        // resident CTAs per SM of the fused kernels
 };
@@ -164,6 +170,7 @@ void materialise(const std::vector<TfHost>& tfs, std::vector<float>* params, std
       }
     } else if (t.kind == ADJ_ADJ_POST_BLOCK || t.kind == ADJ_ADJ_DENSE) {
       d.kt = t.kt;
+      d.k = t.k;
       while (params->size() % 4) params->push_back(0.f);
       d.q_off = (uint32_t)params->size();
       for (int i = 0; i < t.kt; ++i)
@@ -217,6 +224,8 @@ void free_blocks(adj_plan* p) {
   cudaFree(p->d_tile_blk);
   cudaFree(p->d_range_begin);
   cudaFree(p->d_plain);
+  cudaFree(p->d_tile_side);
+  p->d_tile_side = nullptr;
   p->d_plain = nullptr;
   p->plain.clear();
   p->d_tiles = nullptr;
@@ -252,6 +261,32 @@ int run(adj_plan* p, bool inverse, const void* in, float* out, cudaStream_t stre
   a.n_ranges = p->n_ranges;
   cudaError_t e = launch_fused(inverse, p->threads, inverse ? p->grid_inv : p->grid_fwd, a, stream);
   if (e != cudaSuccess) return cuda_fail(e, inverse ? "inverse launch" : "forward launch");
+  return ADJ_OK;
+}
+
+int run_multi(adj_plan* p, const int16_t* in, float* out, float* side, cudaStream_t stream) {
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  if (!p->multi) return fail(ADJ_ERR_INVALID_ARG, "adj_plan_prepare_multiple has not been called for this block list");
+  int rc;
+  if ((rc = check_ptr(in, "input")) || (rc = check_ptr(out, "output"))) return rc;
+  if (p->side_off.back() > 0 && (rc = check_ptr(side, "side buffer"))) return rc;
+  if (p->n_tiles == 0) return ADJ_OK;
+  FusedArgs a{};
+  a.tiles = p->d_tiles;
+  a.tile_blk = p->d_tile_blk;
+  a.tfs = p->d_tfs;
+  a.params = p->d_params;
+  a.in = in;
+  a.out = out;
+  a.sched = p->d_sched + 2;
+  a.range_begin = p->d_range_begin;
+  a.n_tiles = p->n_tiles;
+  a.n_ranges = p->n_ranges;
+  a.side = side;
+  a.tile_side = p->d_tile_side;
+  cudaError_t e = launch_multi(p->grid_multi, a, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "Multiple forward launch");
   return ADJ_OK;
 }
 
@@ -352,6 +387,7 @@ void apply_grid(adj_plan* p) {
   const int c = p->tuning.ctas_per_sm;
   p->grid_fwd = std::max(1, c > 0 ? std::min(c, p->occ_fwd) : p->occ_fwd) * p->n_sm;
   p->grid_inv = std::max(1, c > 0 ? std::min(c, p->occ_inv) : p->occ_inv) * p->n_sm;
+  p->grid_multi = std::max(1, c > 0 ? std::min(c, p->occ_multi) : p->occ_multi) * p->n_sm;
 }
 
 // Tiles, per-SM ranges and the plain form's per-size lists for the plan's block list,
@@ -361,7 +397,7 @@ int build_layout(adj_plan* p) {
   // class by class so that consecutive tiles run the same code: the order is by block size,
   // then by the code-determining (core, kind) of each direction, then by transform index.
   struct Open {
-    std::vector<uint32_t> offs;
+    std::vector<uint32_t> offs, sides;
     int64_t first;
   };
   std::unordered_map<uint64_t, Open> open;
@@ -369,7 +405,7 @@ int build_layout(adj_plan* p) {
     uint64_t key;
     int64_t first;
     TileDev t;
-    std::vector<uint32_t> offs;
+    std::vector<uint32_t> offs, sides;
   };
   std::vector<Done> done;
   auto emit = [&](uint64_t key, Open& o) {
@@ -383,13 +419,16 @@ int build_layout(adj_plan* p) {
     d.t.tf_v = (uint16_t)key;
     d.t.nblk = (uint16_t)o.offs.size();
     d.offs.swap(o.offs);
+    d.sides.swap(o.sides);
     done.push_back(std::move(d));
   };
-  for (const adj_block_t& b : p->blocks) {
+  for (size_t i = 0; i < p->blocks.size(); ++i) {
+    const adj_block_t& b = p->blocks[i];
     const uint64_t key = ((uint64_t)b.w << 48) | ((uint64_t)b.h << 32) | ((uint64_t)b.tf_h << 16) | b.tf_v;
     Open& o = open[key];
     if (o.offs.empty()) o.first = b.offset;
     o.offs.push_back((uint32_t)(b.offset / 16));
+    if (p->multi) o.sides.push_back((uint32_t)(p->side_off[p->orig[i]] / 4));
     if ((int)o.offs.size() >= tuned_capacity(p, b.w, b.h)) emit(key, o);
   }
   for (auto& kv : open)
@@ -405,18 +444,24 @@ int build_layout(adj_plan* p) {
     return a.key != b.key ? a.key < b.key : a.first < b.first;
   });
   std::vector<TileDev> tiles;
-  std::vector<uint32_t> tblk;
+  std::vector<uint32_t> tblk, tside;
   tiles.reserve(done.size());
   tblk.reserve(p->blocks.size());
   // Each tile's block list starts on a 16-byte boundary and the list ends with 4 spare
-  // entries: the kernel fetches a tile's offsets with 16-byte asynchronous copies.
+  // entries: the kernel fetches a tile's offsets with 16-byte asynchronous copies.  The
+  // side offsets of the Multiple form follow the same indexing.
   for (Done& d : done) {
     while (tblk.size() % 4) tblk.push_back(0u);
     d.t.blk_begin = (uint32_t)tblk.size();
     tiles.push_back(d.t);
     tblk.insert(tblk.end(), d.offs.begin(), d.offs.end());
+    if (p->multi) {
+      tside.resize(d.t.blk_begin, 0u);
+      tside.insert(tside.end(), d.sides.begin(), d.sides.end());
+    }
   }
   tblk.resize(tblk.size() + 4, 0u);
+  if (p->multi) tside.resize(tblk.size(), 0u);
 
   // Per-SM ranges of the sorted tile list with about equal numbers of coefficients.
   const int n_ranges = tiles.empty() ? 0 : (int)std::min<size_t>({(size_t)std::max(1, p->n_sm * std::max(1, p->tuning.ranges_per_sm)), (size_t)kMaxRanges, tiles.size()});
@@ -463,6 +508,10 @@ int build_layout(adj_plan* p) {
     CUDA_TRY(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(p->d_tile_blk, tblk.data(), tblk.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(p->d_range_begin, rbeg.data(), rbeg.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+    if (p->multi) {
+      CUDA_TRY(cudaMalloc(&p->d_tile_side, tside.size() * sizeof(uint32_t)));
+      CUDA_TRY(cudaMemcpy(p->d_tile_side, tside.data(), tside.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
   }
   p->n_ranges = n_ranges;
   p->n_tiles = (int)tiles.size();
@@ -484,7 +533,7 @@ int adj_graph_create(adj_plan_t* p, int32_t what, const void* d_in, float* d_out
   if (!graph) return fail(ADJ_ERR_INVALID_ARG, "null graph pointer");
   *graph = nullptr;
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
-  if (what < ADJ_GRAPH_FWD || what > ADJ_GRAPH_ROUNDTRIP) return fail(ADJ_ERR_INVALID_ARG, "unknown graph kind %d", what);
+  if (what < ADJ_GRAPH_FWD || what > ADJ_GRAPH_FWD_MULTIPLE) return fail(ADJ_ERR_INVALID_ARG, "unknown graph kind %d", what);
   if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
   int rc;
   if ((rc = check_ptr(d_in, "input")) || (rc = check_ptr(d_out, "output"))) return rc;
@@ -501,6 +550,7 @@ int adj_graph_create(adj_plan_t* p, int32_t what, const void* d_in, float* d_out
     case ADJ_GRAPH_INV: rc = run(p, true, d_in, d_out, s); break;
     case ADJ_GRAPH_FWD_PLAIN: rc = run_plain(p, false, d_in, d_out, s); break;
     case ADJ_GRAPH_INV_PLAIN: rc = run_plain(p, true, d_in, d_out, s); break;
+    case ADJ_GRAPH_FWD_MULTIPLE: rc = run_multi(p, static_cast<const int16_t*>(d_in), d_out, d_out2, s); break;
     default:
       rc = run(p, false, d_in, d_out, s);
       if (!rc) rc = run(p, true, d_out, d_out2, s);
@@ -587,8 +637,8 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     if (e != cudaSuccess) rc = cuda_fail(e, "gradient layout upload");
   }
   if (!rc) {
-    e = cudaMalloc(&p->d_sched, 2 * sizeof(SchedState));
-    if (e == cudaSuccess) e = cudaMemset(p->d_sched, 0, 2 * sizeof(SchedState));
+    e = cudaMalloc(&p->d_sched, 3 * sizeof(SchedState));
+    if (e == cudaSuccess) e = cudaMemset(p->d_sched, 0, 3 * sizeof(SchedState));
     if (e != cudaSuccess) rc = cuda_fail(e, "scheduler state allocation");
   }
   for (int inv = 0; inv < 2 && !rc; ++inv) {
@@ -598,6 +648,14 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
     if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
     else (inv ? p->occ_inv : p->occ_fwd) = std::max(1, occ);
+  }
+  if (!rc) {
+    const void* fn = multi_kernel_ptr();
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
+    if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
+    else p->occ_multi = std::max(1, occ);
   }
   if (!rc) {
     for (int i = 0; i < 25; ++i) p->tuning.cap_div[i] = 1;
@@ -660,6 +718,9 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
   p->blocks.clear();
   p->blocks.reserve(n_blocks);
   for (int64_t i : order) p->blocks.push_back(blocks[i]);
+  p->orig = order;
+  p->multi = false;
+  p->side_off.clear();
   p->n_blocks = n_blocks;
   p->total = total_coefs;
   const int rc = build_layout(p);
@@ -676,6 +737,49 @@ int adj_transform_fwd(adj_plan_t* p, const int16_t* d_resid, float* d_coef, void
 int adj_transform_inv(adj_plan_t* p, const float* d_coef, float* d_resid_out, void* stream) {
   g_err.clear();
   return run(p, true, d_coef, d_resid_out, static_cast<cudaStream_t>(stream));
+}
+
+int adj_plan_prepare_multiple(adj_plan_t* p, int64_t* side_offsets, int64_t* side_total) {
+  g_err.clear();
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  auto k_of = [&](int t) { return p->tfs[t].kind == ADJ_ADJ_POST_BLOCK ? p->tfs[t].k : 0; };
+  std::vector<int64_t> size(p->blocks.size());
+  for (size_t s = 0; s < p->blocks.size(); ++s) {
+    const adj_block_t& b = p->blocks[s];
+    for (int t : {(int)b.tf_h, (int)b.tf_v}) {
+      const TfHost& tf = p->tfs[t];
+      if (tf.core != ADJ_CORE_DCT2 || (tf.kind != ADJ_ADJ_NONE && tf.kind != ADJ_ADJ_POST_BLOCK))
+        return fail(ADJ_ERR_INVALID_ARG, "block %lld: transform %d is not a DCT-2 with no adjustment or a post-adjustment",
+                    (long long)p->orig[s], t);
+      if (2 * k_of(t) > tf.n)
+        return fail(ADJ_ERR_UNSUPPORTED_SIZE, "block %lld: transform %d has K=%d > n/2", (long long)p->orig[s], t, tf.k);
+    }
+    const int64_t kh = k_of(b.tf_h), kv = k_of(b.tf_v);
+    size[p->orig[s]] = (2 * kv * b.w + 2 * b.h * kh + 3) / 4 * 4;
+  }
+  std::vector<int64_t> off(p->blocks.size() + 1, 0);
+  for (size_t i = 0; i < size.size(); ++i) off[i + 1] = off[i] + size[i];
+  if (off.back() / 4 > (int64_t)UINT32_MAX) return fail(ADJ_ERR_INVALID_ARG, "side buffer of %lld floats is too large", (long long)off.back());
+  const bool was = p->multi;
+  std::vector<int64_t> old;
+  old.swap(p->side_off);
+  p->side_off = off;
+  p->multi = true;
+  const int rc = build_layout(p);
+  if (rc) {
+    p->multi = was;
+    p->side_off.swap(old);
+    return rc;
+  }
+  if (side_offsets) std::copy(off.begin(), off.end(), side_offsets);
+  if (side_total) *side_total = off.back();
+  return ADJ_OK;
+}
+
+int adj_transform_fwd_multiple(adj_plan_t* p, const int16_t* d_resid, float* d_coef, float* d_side, void* stream) {
+  g_err.clear();
+  return run_multi(p, d_resid, d_coef, d_side, static_cast<cudaStream_t>(stream));
 }
 
 int adj_transform_bwd(adj_plan_t* p, const void* d_x, int32_t x_dtype, const float* d_gy, float* d_gx,

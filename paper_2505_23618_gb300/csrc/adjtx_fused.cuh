@@ -124,6 +124,182 @@ __device__ __forceinline__ void col_dispatch(const TfDev& tf, const float* __res
   }
 }
 
+// ---------------------------------------------------------------------------------
+// "Multiple" forward (Section 2.3): the 2-D DCT-2 of every block plus the coefficients
+// of the four (vertical, horizontal) pairings of DST-7 and DCT-8 post-adjustments that
+// differ from it.  Every transform is a DCT-2, optionally followed by C = diag(Q, I) with
+// K <= n/2 (the DST-7 adjustment); the DCT-8 one is S C S (Eq. 5).  Side regions of one
+// block, in floats from its side offset, each row-major (kh, kv: horizontal and vertical
+// K, 0 without an adjustment; a, b = 0 for DST-7, 1 for DCT-8):
+//   R_a   rows < kv, columns >= kh of the pairings with vertical a:  kv x (w - kh)
+//   L_b   rows >= kv, columns < kh of the pairings with horizontal b: (h - kv) x kh
+//   X_ab  rows < kv, columns < kh of pairing (a, b):                 kv x kh
+// in the order R_0, R_1, L_0, L_1, X_00, X_01, X_10, X_11.
+// ---------------------------------------------------------------------------------
+struct SideLayout {
+  int w, h, kh, kv;
+  __device__ __forceinline__ int r(int a) const { return a * kv * (w - kh); }
+  __device__ __forceinline__ int l(int b) const { return 2 * kv * (w - kh) + b * (h - kv) * kh; }
+  __device__ __forceinline__ int x(int a, int b) const {
+    return 2 * kv * (w - kh) + 2 * (h - kv) * kh + (2 * a + b) * kv * kh;
+  }
+};
+
+// First k outputs of both adjustments of a DCT-2 line v, from one pass over the padded
+// KT x KT Q: with e_i = sum over even j of Q[i][j] v_j and o_i = the sum over odd j, the
+// DST-7 adjustment gives e_i + o_i and the DCT-8 one, (S Q S v)_i, gives (-1)^i (e_i - o_i).
+// emit(i, dst7_i, dct8_i) is called for i < k.
+template <int N, int KT, class Emit>
+__device__ __forceinline__ void split_post_k(const float (&v)[N], const TfDev& tf, const float* __restrict__ P,
+                                             int k, const Emit& emit) {
+  constexpr int R = PostRows<KT, float>::R;
+#pragma unroll 1
+  for (int i = 0; i < k; i += R) {
+    float e[R], o[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) e[r] = o[r] = 0.f;
+#pragma unroll
+    for (int g = 0; g < KT / 4; ++g) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float q[4];
+        q_quad(P, tf, i + r, g, q);
+        e[r] = fmaf(q[0], v[4 * g], e[r]);
+        o[r] = fmaf(q[1], v[4 * g + 1], o[r]);
+        e[r] = fmaf(q[2], v[4 * g + 2], e[r]);
+        o[r] = fmaf(q[3], v[4 * g + 3], o[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int ii = i + r;
+      if (ii < k) emit(ii, e[r] + o[r], (ii & 1) ? o[r] - e[r] : e[r] - o[r]);
+    }
+  }
+}
+
+// K <= n/2, so the padded size is at most max(4, n/2).
+template <int N, class Emit>
+__device__ __forceinline__ void split_post(const float (&v)[N], const TfDev& tf, const float* __restrict__ P, int k,
+                                           const Emit& emit) {
+  switch (tf.kt) {
+    case 4: split_post_k<N, 4>(v, tf, P, k, emit); break;
+    case 8: if constexpr (N >= 16) { split_post_k<N, 8>(v, tf, P, k, emit); } break;
+    case 16: if constexpr (N >= 32) { split_post_k<N, 16>(v, tf, P, k, emit); } break;
+    default: if constexpr (N >= 64) { split_post_k<N, 32>(v, tf, P, k, emit); } break;
+  }
+}
+
+// Column pass over the DCT-2 rows: the 2-D DCT-2 of every column, and for the columns
+// >= kh the first kv outputs of both vertical adjustments (regions R_0, R_1).
+template <int H, int W, int THREADS>
+__device__ __forceinline__ void multi_col_dct(const TfDev& tv, const float* __restrict__ P, const float* buf,
+                                              const uint32_t* sOff, const uint32_t* sSide, float* __restrict__ out,
+                                              float* __restrict__ side, int nb, int kh, int kv) {
+  constexpr int lgw = ilog2(W);
+  const int nlines = nb * W, wr = W - kh;
+  for (int l = threadIdx.x; l < nlines; l += THREADS) {
+    const int b = l >> lgw, c = l & (W - 1);
+    float v[H];
+    ColSw<W>(buf + b * (W * H), c).template load<H>(v);
+    Core<H, 0>::apply(v);
+    DstGCol<W>{out + (size_t)sOff[b] * 16 + c}.template store<H>(v);
+    if (kv > 0 && c >= kh) {
+      float* r0 = side + (size_t)sSide[b] * 4 + (c - kh);
+      float* r1 = r0 + kv * wr;
+      split_post<H>(v, tv, P, kv, [&](int i, float s7, float c8) {
+        r0[i * wr] = s7;
+        r1[i * wr] = c8;
+      });
+    }
+  }
+}
+
+// Row step: the first kh outputs of both horizontal adjustments of every DCT-2 row,
+// written over the row's columns 0..2kh-1 (DST-7 first), which the column pass above has
+// finished reading.
+template <int W, int KT, int THREADS>
+__device__ __forceinline__ void multi_row_adjust_k(const TfDev& th, const float* __restrict__ P, float* buf, int nb,
+                                                   int h, int kh) {
+  constexpr int SH = sw_shift(W), MK = sw_mask(W);
+  const int nlines = nb * h;
+  for (int l = threadIdx.x; l < nlines; l += THREADS) {
+    const RowSw row{buf + l * W, ((l & (h - 1)) >> SH) & MK};
+    float v[KT];
+    row.template load<KT>(v);
+    split_post_k<KT, KT>(v, th, P, kh, [&](int i, float s7, float c8) {
+      row.put_rt(i, s7);
+      row.put_rt(kh + i, c8);
+    });
+  }
+}
+
+template <int W, int THREADS>
+__device__ __forceinline__ void multi_row_adjust(const TfDev& th, const float* __restrict__ P, float* buf, int nb,
+                                                 int h, int kh) {
+  switch (th.kt) {
+    case 4: multi_row_adjust_k<W, 4, THREADS>(th, P, buf, nb, h, kh); break;
+    case 8: if constexpr (W >= 16) { multi_row_adjust_k<W, 8, THREADS>(th, P, buf, nb, h, kh); } break;
+    case 16: if constexpr (W >= 32) { multi_row_adjust_k<W, 16, THREADS>(th, P, buf, nb, h, kh); } break;
+    default: if constexpr (W >= 64) { multi_row_adjust_k<W, 32, THREADS>(th, P, buf, nb, h, kh); } break;
+  }
+}
+
+// Column pass over the horizontally adjusted columns (2kh per block): vertical DCT-2,
+// rows >= kv to L_b, and the first kv outputs of both vertical adjustments to X_0b, X_1b.
+template <int H, int W, int THREADS>
+__device__ __forceinline__ void multi_col_adj(const TfDev& tv, const float* __restrict__ P, const float* buf,
+                                              const uint32_t* sSide, float* __restrict__ side, int nb, int kh,
+                                              int kv) {
+  const int per = 2 * kh, nlines = nb * per;
+  const SideLayout L{W, H, kh, kv};
+  for (int l = threadIdx.x; l < nlines; l += THREADS) {
+    const int b = l / per, c = l - b * per;
+    const int hb = c >= kh ? 1 : 0, j = c - hb * kh;
+    float v[H];
+    ColSw<W>(buf + b * (W * H), c).template load<H>(v);
+    Core<H, 0>::apply(v);
+    float* sb = side + (size_t)sSide[b] * 4;
+    float* lb = sb + L.l(hb) + j;  // row i >= kv of L_b at lb[(i - kv) * kh]
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+      if (i >= kv) lb[(i - kv) * kh] = v[i];
+    if (kv > 0) {
+      float* x0 = sb + L.x(0, hb) + j;
+      float* x1 = sb + L.x(1, hb) + j;
+      split_post<H>(v, tv, P, kv, [&](int i, float s7, float c8) {
+        x0[i * kh] = s7;
+        x1[i * kh] = c8;
+      });
+    }
+  }
+}
+
+template <int H, int THREADS>
+__device__ __forceinline__ void multi_after_rows(const TfDev& th, const TfDev& tv, const float* __restrict__ P,
+                                                 float* buf, const uint32_t* sOff, const uint32_t* sSide,
+                                                 float* __restrict__ out, float* __restrict__ side, int nb, int w) {
+  const int kh = th.kind == KIND_POST ? th.k : 0, kv = tv.kind == KIND_POST ? tv.k : 0;
+#define ADJ_MULTI_W(W)                                                                    \
+  {                                                                                       \
+    multi_col_dct<H, W, THREADS>(tv, P, buf, sOff, sSide, out, side, nb, kh, kv);         \
+    if (kh > 0) {                                                                         \
+      __syncthreads();                                                                    \
+      multi_row_adjust<W, THREADS>(th, P, buf, nb, H, kh);                                \
+      __syncthreads();                                                                    \
+      multi_col_adj<H, W, THREADS>(tv, P, buf, sSide, side, nb, kh, kv);                  \
+    }                                                                                     \
+  }
+  switch (w) {
+    case 4: ADJ_MULTI_W(4) break;
+    case 8: ADJ_MULTI_W(8) break;
+    case 16: ADJ_MULTI_W(16) break;
+    case 32: ADJ_MULTI_W(32) break;
+    default: ADJ_MULTI_W(64) break;
+  }
+#undef ADJ_MULTI_W
+}
+
 // Shared memory limits residency to kSmemCtasPerSm CTAs per SM; the register budget
 // follows from that, so spills are never traded for occupancy that smem forbids.
 constexpr int kSmemCtasPerSm = (227 * 1024) / (kSmemBytes + 3072);
@@ -136,20 +312,29 @@ __device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes
     cp_async16(static_cast<unsigned char*>(dst) + i, static_cast<const unsigned char*>(src) + i);
 }
 
-template <bool INV, int THREADS>
+template <bool INV, int THREADS, bool MULTI = false>
 __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_kernel(FusedArgs a) {
+  static_assert(!(INV && MULTI), "the Multiple form is forward only");
   extern __shared__ __align__(16) unsigned char smem[];
-  // block offsets / 16 of the tiles in buf[0], buf[1]; a tile's list starts at entry
-  // blk_begin & 3 (it is copied from the 16-byte aligned address below blk_begin)
-  __shared__ __align__(16) uint32_t sOff[2][kMaxTileBlocks + 4];
-  __shared__ __align__(16) TfDev sTf[2][2];                   // (horizontal, vertical) records
-  __shared__ __align__(16) TileDev sDesc[3];                  // descriptors, by tile sequence mod 3
+  // Records of this CTA's tiles, by the tile's sequence number k in the CTA:
+  //   sDesc[k % 4]   descriptor (k .. k+2 are valid at the top of iteration k; k+3 arrives)
+  //   sOff[k % 3]    block offsets / 16 (k, k+1 valid; k+2 arrives); a tile's list starts at
+  //                  entry blk_begin & 3 (it is copied from the 16-byte aligned address below)
+  //   sTf[k % 2]     (horizontal, vertical) transform records (k valid; k+1 arrives)
+  //   sSide[k % 2]   Multiple form: side offsets / 4, indexed like sOff (k valid; k+1 arrives)
+  // and tile k's data in buffer k % 2 while tile k+1 is being copied into the other one.
+  __shared__ __align__(16) uint32_t sOff[3][kMaxTileBlocks + 4];
+  __shared__ __align__(16) uint32_t sSide[MULTI ? 2 : 1][MULTI ? kMaxTileBlocks + 4 : 4];
+  __shared__ __align__(16) TfDev sTf[2][2];
+  __shared__ __align__(16) TileDev sDesc[4];
   __shared__ int sIdx[3];
   const int tid = threadIdx.x;
   int range = -1;        // thread 0 only: the range claims come from
   unsigned claim_k = 0;  // thread 0 only: pending claim
+  auto list_bytes = [](const TileDev& d) { return (((d.blk_begin & 3) + d.nblk + 3) / 4) * 16; };
 
-  // Prologue: claim three tiles, fetch what the first iteration needs, stage tile 0.
+  // Prologue: claim three tiles; fetch the records of tile 0, stage it, and start fetching
+  // the offsets of tile 1 and the descriptor of tile 2.
   if (tid == 0) {
     sIdx[0] = grab_tile(a.sched, a.range_begin, a.n_ranges, range);
     sIdx[1] = sIdx[0] >= 0 ? grab_tile(a.sched, a.range_begin, a.n_ranges, range) : -1;
@@ -161,33 +346,48 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
     const TileDev d0 = a.tiles[t];
     if (tid == 0) {
       sDesc[0] = d0;
-      if (tn >= 0) sDesc[1] = a.tiles[tn];
       sTf[0][0] = a.tfs[d0.tf_h];
       sTf[0][1] = a.tfs[d0.tf_v];
     }
     for (int b = tid; b < d0.nblk; b += THREADS) sOff[0][(d0.blk_begin & 3) + b] = a.tile_blk[d0.blk_begin + b];
+    if constexpr (MULTI) {
+      for (int b = tid; b < d0.nblk; b += THREADS) sSide[0][(d0.blk_begin & 3) + b] = a.tile_side[d0.blk_begin + b];
+    }
     __syncthreads();
     stage_tile<INV, THREADS>(d0, sOff[0] + (d0.blk_begin & 3), a.in, reinterpret_cast<float*>(smem));
-    if (tn2 >= 0) copy_async<THREADS>(&sDesc[2], a.tiles + tn2, sizeof(TileDev));
+    if (tn >= 0) {
+      const TileDev d1 = a.tiles[tn];
+      if (tid == 0) sDesc[1] = d1;
+      copy_async<THREADS>(sOff[1], a.tile_blk + (d1.blk_begin & ~3u), list_bytes(d1));
+    }
+    if (tn2 >= 0 && tid == 0) cp_async16(&sDesc[2], a.tiles + tn2);
     cp_async_commit();
   }
 
-  // Per tile: (1) wait; (2) async-fetch the next tile's metadata; (3) row pass; (4) wait,
-  // barrier; (5) stage the next tile; (6) column pass.  Copies of the next tile overlap
-  // the column pass of this one and the row pass of the next.
-  for (int k = 0, cur = 0; t >= 0; ++k, cur ^= 1) {
+  // Per tile k: (1) wait for everything fetched during the previous iteration, barrier;
+  // (2) start copying tile k+1 into the other buffer, with its records, and the offsets of
+  // tile k+2; claim tile k+3; (3) row pass; (4) thread 0 resolves the claim and fetches that
+  // tile's descriptor; barrier; (5) column pass.  The copies of tile k+1 overlap both passes
+  // of tile k.
+  for (int k = 0; t >= 0; ++k) {
+    const int cur = k & 1;
     float* buf = reinterpret_cast<float*>(smem + cur * kBufBytes);
-    // (1) this tile's data, the next descriptor and this tile's records have landed
+    // (1)
     cp_async_wait_all();
     __syncthreads();
-    const TileDev td = sDesc[k % 3];
-    // (2) fetch the next tile's block offsets and records; claim one more tile
+    const TileDev td = sDesc[k & 3];
+    // (2)
     if (tn >= 0) {
-      const TileDev dn = sDesc[(k + 1) % 3];
-      copy_async<THREADS>(sOff[cur ^ 1], a.tile_blk + (dn.blk_begin & ~3u),
-                          (((dn.blk_begin & 3) + dn.nblk + 3) / 4) * 16);
+      const TileDev dn = sDesc[(k + 1) & 3];
+      stage_tile<INV, THREADS>(dn, sOff[(k + 1) % 3] + (dn.blk_begin & 3), a.in,
+                               reinterpret_cast<float*>(smem + (cur ^ 1) * kBufBytes));
       copy_async<THREADS>(&sTf[cur ^ 1][0], a.tfs + dn.tf_h, sizeof(TfDev));
       copy_async<THREADS>(&sTf[cur ^ 1][1], a.tfs + dn.tf_v, sizeof(TfDev));
+      if constexpr (MULTI) copy_async<THREADS>(sSide[cur ^ 1], a.tile_side + (dn.blk_begin & ~3u), list_bytes(dn));
+    }
+    if (tn2 >= 0) {
+      const TileDev dn2 = sDesc[(k + 2) & 3];
+      copy_async<THREADS>(sOff[(k + 2) % 3], a.tile_blk + (dn2.blk_begin & ~3u), list_bytes(dn2));
     }
     cp_async_commit();
     if (tid == 0 && tn2 >= 0) claim_k = atomicAdd(&a.sched->pos[range], 1u);
@@ -195,7 +395,8 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
     // (3) row pass (horizontal transform, length w), in place
     const int w = td.w, h = td.h, nb = td.nblk;
     {
-      const TfDev tf = sTf[cur][0];
+      TfDev tf = sTf[cur][0];
+      if constexpr (MULTI) tf.kind = KIND_NONE;  // the rows get the plain DCT-2 first
       switch (w) {
         case 4: row_pass<4, INV, THREADS>(tf, a.params, buf, nb, h); break;
         case 8: row_pass<8, INV, THREADS>(tf, a.params, buf, nb, h); break;
@@ -204,23 +405,29 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
         default: row_pass<64, INV, THREADS>(tf, a.params, buf, nb, h); break;
       }
     }
-    // (4) the next tile's offsets have landed; publish the claimed tile index
-    cp_async_wait_all();
-    if (tid == 0) sIdx[k % 3] = tn2 >= 0 ? claim_resolve(a.sched, a.range_begin, a.n_ranges, range, claim_k) : -1;
-    __syncthreads();
-    const int tn3 = sIdx[k % 3];
-    // (5) stage the next tile into the other buffer; fetch the descriptor after it
-    if (tn >= 0) {
-      const TileDev dn = sDesc[(k + 1) % 3];
-      stage_tile<INV, THREADS>(dn, sOff[cur ^ 1] + (dn.blk_begin & 3), a.in,
-                               reinterpret_cast<float*>(smem + (cur ^ 1) * kBufBytes));
+    // (4) sIdx[0] is free: every thread read it after the previous iteration's barrier (4)
+    if (tid == 0) {
+      const int t3 = tn2 >= 0 ? claim_resolve(a.sched, a.range_begin, a.n_ranges, range, claim_k) : -1;
+      sIdx[0] = t3;
+      if (t3 >= 0) cp_async16(&sDesc[(k + 3) & 3], a.tiles + t3);
+      cp_async_commit();
     }
-    if (tn3 >= 0) copy_async<THREADS>(&sDesc[k % 3], a.tiles + tn3, sizeof(TileDev));
-    cp_async_commit();
-    // (6) column pass (vertical transform, length h), stores to global memory
-    {
+    __syncthreads();
+    const int tn3 = sIdx[0];
+    // (5) column pass (vertical transform, length h), stores to global memory
+    const uint32_t* offs = sOff[k % 3] + (td.blk_begin & 3);
+    if constexpr (MULTI) {
+      const uint32_t* sides = sSide[cur] + (td.blk_begin & 3);
+      const TfDev th = sTf[cur][0], tv = sTf[cur][1];
+      switch (h) {
+        case 4: multi_after_rows<4, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
+        case 8: multi_after_rows<8, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
+        case 16: multi_after_rows<16, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
+        case 32: multi_after_rows<32, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
+        default: multi_after_rows<64, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
+      }
+    } else {
       const TfDev tf = sTf[cur][1];
-      const uint32_t* offs = sOff[cur] + (td.blk_begin & 3);
       switch (h) {
         case 4: col_dispatch<4, INV, THREADS>(tf, a.params, buf, offs, a.out, nb, w); break;
         case 8: col_dispatch<8, INV, THREADS>(tf, a.params, buf, offs, a.out, nb, w); break;

@@ -19,6 +19,9 @@ struct FusedArgs {
   const unsigned* range_begin;  // n_ranges + 1 tile indices
   int n_tiles;
   int n_ranges;
+  // Multiple forward only: side buffer and the side offsets / 4, parallel to tile_blk
+  float* side;
+  const uint32_t* tile_side;
 };
 
 // Plain (unfused) form: the blocks of one size class, each with its own transforms.
@@ -54,6 +57,8 @@ cudaError_t launch_bwd(bool i16, int grid, const BwdArgs& args, double* M, const
                        const int* m_off, const int* g_off, const int* kq, float* gparams, cudaStream_t stream);
 
 const void* fused_kernel_ptr(bool inverse, int threads);
+const void* multi_kernel_ptr();
+cudaError_t launch_multi(int grid, const FusedArgs& args, cudaStream_t stream);
 const void* fused_fwd_ptr();
 const void* fused_inv_ptr();
 void set_last_error(const char* msg);

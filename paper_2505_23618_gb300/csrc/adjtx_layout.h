@@ -28,8 +28,10 @@ struct TfDev {
   uint32_t q_off;     // float index of the kt x kt row-major padded Q (16-B aligned)
   uint32_t cs2_off;   // float4 index of {c, c, s, s} per rotation (packed line pairs, n <= 32)
   uint32_t q2_off;    // float index of Q with every entry duplicated (packed line pairs, n <= 32)
+  int32_t k;          // post / dense: K (the unpadded size of Q); 0 otherwise
+  uint32_t pad[3];
 };
-static_assert(sizeof(TfDev) == 48, "TfDev layout");
+static_assert(sizeof(TfDev) == 64, "TfDev layout");
 
 // A tile: blocks of one (w, h, tf_h, tf_v) class processed together by one CTA.
 struct TileDev {

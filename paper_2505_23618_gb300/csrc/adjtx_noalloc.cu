@@ -134,6 +134,7 @@ int pack_tf(const adj_1d_desc_t* d, const char* name, TfDev* rec, float* params,
   } else if (d->kind == ADJ_ADJ_POST_BLOCK || d->kind == ADJ_ADJ_DENSE) {
     const int k = d->k;
     if (k < 1 || k > d->n) return err(ADJ_ERR_UNSUPPORTED_SIZE, "%s: K=%d with n=%d", name, k, d->n);
+    rec->k = k;
     if (!d->q) return err(ADJ_ERR_INVALID_ARG, "%s: null q", name);
     double worst = 0.0;
     for (int i = 0; i < k; ++i)

@@ -191,17 +191,14 @@ def mixed_tf_table(rng):
 _CTU_P = np.array([1 / 6, 1 / 6, 1 / 6, 0.35, 0.15])
 
 
-def config3(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 2160) -> Workload:
-    """Frames tiled into CTUs of 64x64 with per-CTU block sizes, per-block types.
+def _ctu_sizes(rng, frames: int, width: int, height: int):
+    """Block widths and heights of frames tiled into 64x64 CTUs, per-CTU sizes.
 
     W and H are drawn per CTU from {4,...,64} (P(64)=.15, P(32)=.35, rest 1/6);
     the CTU is tiled uniformly by W x H blocks in raster order.  A partial CTU
     row at the bottom (2160 = 33*64 + 48) is split into power-of-two regions
-    (32 then 16) with H clamped to the region height.  Each block draws its
-    horizontal and vertical (core, kind) uniformly from the 12 combinations.
+    (32 then 16) with H clamped to the region height.
     """
-    rng = np.random.default_rng(seed)
-    tfs, ids = mixed_tf_table(rng)
     cols = width // 64
     full_rows, rem = divmod(height, 64)
     regions = []                      # heights of the bottom strip regions
@@ -224,8 +221,17 @@ def config3(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 216
                     n = (64 // W) * (rh // hh)
                     ws.extend([W] * n)
                     hs.extend([hh] * n)
-    w = np.array(ws)
-    h = np.array(hs)
+    return np.array(ws), np.array(hs)
+
+
+def config3(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 2160) -> Workload:
+    """Frames tiled into CTUs of 64x64 with per-CTU block sizes (``_ctu_sizes``),
+    per-block types: each block draws its horizontal and vertical (core, kind)
+    uniformly from the 12 combinations.
+    """
+    rng = np.random.default_rng(seed)
+    tfs, ids = mixed_tf_table(rng)
+    w, h = _ctu_sizes(rng, frames, width, height)
     nb = w.size
     ch = rng.integers(0, 4, nb)
     kh = rng.integers(0, 3, nb)
@@ -241,6 +247,27 @@ def config3(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 216
     return Workload(f"config3-mixed-{frames}x{width}x{height}", blocks, data, tfs, 1023,
                     f"{frames} frames {width}x{height} tiled by per-CTU sizes 4..64, "
                     "per-block core x adjustment in each direction, 10-bit AR(1)")
+
+
+def config3_multiple(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 2160,
+                     k_max: int = 8) -> Workload:
+    """The config-3 frame tiling for the encoder's DST-7 / DCT-8 search (Section 2.3):
+    every block uses, in each direction, a DCT-2 with a post-adjustment of size
+    K = min(k_max, n/2) (the 8 x 8 adjustment at 16 points and more), Q Haar-random per
+    (direction, n).  Same residual statistics as config 3."""
+    rng = np.random.default_rng(seed)
+    tfs, lut = [], {}
+    for d in ("h", "v"):
+        for n in SIZES:
+            lut[d, n] = len(tfs)
+            tfs.append(random_post(rng, n, CORE_DCT2, min(k_max, n // 2)))
+    w, h = _ctu_sizes(rng, frames, width, height)
+    th = np.array([lut["h", int(x)] for x in SIZES])[np.log2(w).astype(int) - 2]
+    tv = np.array([lut["v", int(x)] for x in SIZES])[np.log2(h).astype(int) - 2]
+    blocks, data = _pack((w, h, th, tv), rng, _stats_c2, 1023)
+    return Workload(f"config3-multiple-{frames}x{width}x{height}", blocks, data, tfs, 1023,
+                    f"{frames} frames {width}x{height} tiled by per-CTU sizes 4..64, DCT-2 + "
+                    f"K=min({k_max}, n/2) post-adjustment both ways, 10-bit AR(1)")
 
 
 def config5(seed: int = 5, frames: int = 16, width: int = 7680, height: int = 4320,
