@@ -51,6 +51,17 @@ struct TfHost {
   std::vector<double> q;  // k x k
 };
 
+// Host-buffer path: the offset-sorted block list is cut into chunks of about
+// kHostChunkCoefs coefficients (at most kMaxHostChunks); chunk c's input copy, kernel and
+// output copy run on three streams, so copies of one chunk overlap the kernel of another.
+constexpr int64_t kHostChunkCoefs = 4 << 20;
+constexpr int kMaxHostChunks = 16;
+struct HostChunk {
+  int64_t begin, end;   // samples [begin, end) covered by the chunk's blocks
+  int tile0, n_tiles;   // the chunk's tiles in the host tile list
+  int r0, n_ranges;     // its per-SM ranges in the host range list
+};
+
 }  // namespace
 
 struct adj_plan {
@@ -92,6 +103,15 @@ struct adj_plan {
   int occ_multi = 0, grid_multi = 0;
   adj_tuning_t tuning{};
   int occ_fwd = 0, occ_inv = 0;        // resident CTAs per SM of the fused kernels
+  // host-buffer path (built on first use, dropped with the block layout)
+  std::vector<HostChunk> chunks;
+  bool chunks_valid = false;
+  TileDev* d_ctiles = nullptr;
+  uint32_t* d_ctile_blk = nullptr;
+  unsigned* d_crange = nullptr;
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_k;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
 };
 
 namespace {
@@ -219,7 +239,19 @@ int upload_params(adj_plan* p) {
   return ADJ_OK;
 }
 
+void free_chunks(adj_plan* p) {
+  cudaFree(p->d_ctiles);
+  cudaFree(p->d_ctile_blk);
+  cudaFree(p->d_crange);
+  p->d_ctiles = nullptr;
+  p->d_ctile_blk = nullptr;
+  p->d_crange = nullptr;
+  p->chunks.clear();
+  p->chunks_valid = false;
+}
+
 void free_blocks(adj_plan* p) {
+  free_chunks(p);
   cudaFree(p->d_tiles);
   cudaFree(p->d_tile_blk);
   cudaFree(p->d_range_begin);
@@ -359,22 +391,6 @@ int ensure_host_staging(adj_plan* p) {
   return ADJ_OK;
 }
 
-int run_host(adj_plan* p, bool inverse, const void* h_in, float* h_out, cudaStream_t stream) {
-  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
-  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
-  if (!h_in || !h_out) return fail(ADJ_ERR_INVALID_ARG, "null host buffer");
-  int rc = ensure_host_staging(p);
-  if (rc) return rc;
-  const size_t in_bytes = (size_t)p->total * (inverse ? 4 : 2);
-  const size_t out_bytes = (size_t)p->total * 4;
-  CUDA_TRY(cudaMemcpyAsync(p->d_host_in, h_in, in_bytes, cudaMemcpyHostToDevice, stream));
-  rc = run(p, inverse, p->d_host_in, p->d_host_out, stream);
-  if (rc) return rc;
-  CUDA_TRY(cudaMemcpyAsync(h_out, p->d_host_out, out_bytes, cudaMemcpyDeviceToHost, stream));
-  CUDA_TRY(cudaStreamSynchronize(stream));
-  return ADJ_OK;
-}
-
 }  // namespace
 
 int tuned_capacity(const adj_plan* p, int w, int h) {
@@ -392,10 +408,21 @@ void apply_grid(adj_plan* p) {
 
 // Tiles, per-SM ranges and the plain form's per-size lists for the plan's block list,
 // under the plan's tuning.
-int build_layout(adj_plan* p) {
-  // Tiles: blocks of one (w, h, tf_h, tf_v) class, filled in storage order, then listed
-  // class by class so that consecutive tiles run the same code: the order is by block size,
-  // then by the code-determining (core, kind) of each direction, then by transform index.
+// Host image of a tile list: tiles, their block offsets (and Multiple side offsets) and
+// the per-SM ranges.  blk_begin indexes tblk; range entries index tiles.
+struct TileSet {
+  std::vector<TileDev> tiles;
+  std::vector<uint32_t> tblk, tside;
+  std::vector<unsigned> rbeg;
+  int n_ranges = 0;
+};
+
+// Tiles of the blocks [i0, i1) of the plan's (offset-sorted) list: blocks of one
+// (w, h, tf_h, tf_v) class, filled in storage order, then listed class by class so that
+// consecutive tiles run the same code (by block size, then by the code-determining
+// (core, kind) of each direction, then by transform index); then per-SM ranges of about
+// equal numbers of coefficients.  Block offsets are appended to ts->tblk (4-aligned lists).
+void build_tiles(const adj_plan* p, size_t i0, size_t i1, TileSet* ts) {
   struct Open {
     std::vector<uint32_t> offs, sides;
     int64_t first;
@@ -422,7 +449,7 @@ int build_layout(adj_plan* p) {
     d.sides.swap(o.sides);
     done.push_back(std::move(d));
   };
-  for (size_t i = 0; i < p->blocks.size(); ++i) {
+  for (size_t i = i0; i < i1; ++i) {
     const adj_block_t& b = p->blocks[i];
     const uint64_t key = ((uint64_t)b.w << 48) | ((uint64_t)b.h << 32) | ((uint64_t)b.tf_h << 16) | b.tf_v;
     Open& o = open[key];
@@ -443,10 +470,12 @@ int build_layout(adj_plan* p) {
     if (ka != kb) return ka < kb;
     return a.key != b.key ? a.key < b.key : a.first < b.first;
   });
-  std::vector<TileDev> tiles;
-  std::vector<uint32_t> tblk, tside;
-  tiles.reserve(done.size());
-  tblk.reserve(p->blocks.size());
+  std::vector<TileDev>& tiles = ts->tiles;
+  std::vector<uint32_t>& tblk = ts->tblk;
+  std::vector<uint32_t>& tside = ts->tside;
+  const size_t first_tile = tiles.size();
+  tiles.reserve(first_tile + done.size());
+  tblk.reserve(tblk.size() + (i1 - i0) + 4);
   // Each tile's block list starts on a 16-byte boundary and the list ends with 4 spare
   // entries: the kernel fetches a tile's offsets with 16-byte asynchronous copies.  The
   // side offsets of the Multiple form follow the same indexing.
@@ -463,21 +492,39 @@ int build_layout(adj_plan* p) {
   tblk.resize(tblk.size() + 4, 0u);
   if (p->multi) tside.resize(tblk.size(), 0u);
 
-  // Per-SM ranges of the sorted tile list with about equal numbers of coefficients.
-  const int n_ranges = tiles.empty() ? 0 : (int)std::min<size_t>({(size_t)std::max(1, p->n_sm * std::max(1, p->tuning.ranges_per_sm)), (size_t)kMaxRanges, tiles.size()});
-  std::vector<unsigned> rbeg;
+  // Per-SM ranges of this set's tiles (indices relative to its first tile) with about
+  // equal numbers of coefficients.
+  const size_t nt = tiles.size() - first_tile;
+  const int n_ranges = nt == 0 ? 0 : (int)std::min<size_t>({(size_t)std::max(1, p->n_sm * std::max(1, p->tuning.ranges_per_sm)), (size_t)kMaxRanges, nt});
+  std::vector<unsigned>& rbeg = ts->rbeg;
   if (n_ranges > 0) {
-    std::vector<int64_t> cum(tiles.size() + 1, 0);
-    for (size_t i = 0; i < tiles.size(); ++i) cum[i + 1] = cum[i] + (int64_t)tiles[i].nblk * tiles[i].w * tiles[i].h;
+    std::vector<int64_t> cum(nt + 1, 0);
+    for (size_t i = 0; i < nt; ++i) {
+      const TileDev& t = tiles[first_tile + i];
+      cum[i + 1] = cum[i] + (int64_t)t.nblk * t.w * t.h;
+    }
     rbeg.push_back(0);
     for (int r = 1; r < n_ranges; ++r) {
       const int64_t target = cum.back() * r / n_ranges;
       size_t i = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
       i = std::max<size_t>(i, rbeg.back());
-      rbeg.push_back((unsigned)std::min(i, tiles.size()));
+      rbeg.push_back((unsigned)std::min(i, nt));
     }
-    rbeg.push_back((unsigned)tiles.size());
+    rbeg.push_back((unsigned)nt);
   }
+  ts->n_ranges = n_ranges;
+}
+
+// Tiles, per-SM ranges and the plain form's per-size lists for the plan's block list,
+// under the plan's tuning.
+int build_layout(adj_plan* p) {
+  TileSet ts;
+  build_tiles(p, 0, p->blocks.size(), &ts);
+  const std::vector<TileDev>& tiles = ts.tiles;
+  const std::vector<uint32_t>& tblk = ts.tblk;
+  const std::vector<uint32_t>& tside = ts.tside;
+  const std::vector<unsigned>& rbeg = ts.rbeg;
+  const int n_ranges = ts.n_ranges;
 
   // Plain form: blocks grouped by size, in storage order within a size.
   std::vector<PlainBlock> pblk;
@@ -518,6 +565,104 @@ int build_layout(adj_plan* p) {
   p->has_blocks = true;
   return ADJ_OK;
 }
+
+namespace {
+
+// Chunks of the host-buffer path, their tile lists, streams and events.
+int build_host_chunks(adj_plan* p) {
+  free_chunks(p);
+  const size_t n = p->blocks.size();
+  const int64_t target = std::max<int64_t>(kHostChunkCoefs, (p->total + kMaxHostChunks - 1) / kMaxHostChunks);
+  TileSet ts;
+  for (size_t i = 0; i < n;) {
+    size_t j = i;
+    int64_t coefs = 0;
+    while (j < n && (j == i || coefs < target)) {
+      coefs += (int64_t)p->blocks[j].w * p->blocks[j].h;
+      ++j;
+    }
+    HostChunk c{};
+    c.begin = p->blocks[i].offset;
+    c.end = p->blocks[j - 1].offset + (int64_t)p->blocks[j - 1].w * p->blocks[j - 1].h;
+    c.tile0 = (int)ts.tiles.size();
+    c.r0 = (int)ts.rbeg.size();
+    build_tiles(p, i, j, &ts);
+    c.n_tiles = (int)ts.tiles.size() - c.tile0;
+    c.n_ranges = ts.n_ranges;
+    p->chunks.push_back(c);
+    i = j;
+  }
+  if (!ts.tiles.empty()) {
+    CUDA_TRY(cudaMalloc(&p->d_ctiles, ts.tiles.size() * sizeof(TileDev)));
+    CUDA_TRY(cudaMalloc(&p->d_ctile_blk, ts.tblk.size() * sizeof(uint32_t)));
+    CUDA_TRY(cudaMalloc(&p->d_crange, ts.rbeg.size() * sizeof(unsigned)));
+    CUDA_TRY(cudaMemcpy(p->d_ctiles, ts.tiles.data(), ts.tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p->d_ctile_blk, ts.tblk.data(), ts.tblk.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p->d_crange, ts.rbeg.data(), ts.rbeg.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+  }
+  if (!p->s_in) CUDA_TRY(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
+  if (!p->s_out) CUDA_TRY(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
+  if (!p->ev_start) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
+  if (!p->ev_done) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming));
+  while (p->ev_in.size() < p->chunks.size()) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CUDA_TRY(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    p->ev_in.push_back(a);
+    CUDA_TRY(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    p->ev_k.push_back(b);
+  }
+  p->chunks_valid = true;
+  return ADJ_OK;
+}
+
+// Host buffers: per chunk, input copy on s_in -> kernel on `stream` -> output copy on
+// s_out; the call returns when the last output copy has finished.
+int run_host(adj_plan* p, bool inverse, const void* h_in, float* h_out, cudaStream_t stream) {
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  if (!h_in || !h_out) return fail(ADJ_ERR_INVALID_ARG, "null host buffer");
+  int rc = ensure_host_staging(p);
+  if (rc) return rc;
+  if (!p->chunks_valid && (rc = build_host_chunks(p))) return rc;
+  const size_t in_es = inverse ? 4 : 2;
+  const unsigned char* hin = static_cast<const unsigned char*>(h_in);
+  unsigned char* din = static_cast<unsigned char*>(p->d_host_in);
+  CUDA_TRY(cudaEventRecord(p->ev_start, stream));
+  CUDA_TRY(cudaStreamWaitEvent(p->s_in, p->ev_start, 0));
+  CUDA_TRY(cudaStreamWaitEvent(p->s_out, p->ev_start, 0));
+  for (size_t c = 0; c < p->chunks.size(); ++c) {
+    const HostChunk& ch = p->chunks[c];
+    const size_t n = (size_t)(ch.end - ch.begin);
+    CUDA_TRY(cudaMemcpyAsync(din + ch.begin * in_es, hin + ch.begin * in_es, n * in_es, cudaMemcpyHostToDevice, p->s_in));
+    CUDA_TRY(cudaEventRecord(p->ev_in[c], p->s_in));
+    CUDA_TRY(cudaStreamWaitEvent(stream, p->ev_in[c], 0));
+    if (ch.n_tiles > 0) {
+      FusedArgs a{};
+      a.tiles = p->d_ctiles + ch.tile0;
+      a.tile_blk = p->d_ctile_blk;
+      a.tfs = p->d_tfs;
+      a.params = p->d_params;
+      a.in = p->d_host_in;
+      a.out = p->d_host_out;
+      a.sched = p->d_sched + (inverse ? 1 : 0);
+      a.range_begin = p->d_crange + ch.r0;
+      a.n_tiles = ch.n_tiles;
+      a.n_ranges = ch.n_ranges;
+      const cudaError_t e = launch_fused(inverse, p->threads, inverse ? p->grid_inv : p->grid_fwd, a, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "chunk launch");
+    }
+    CUDA_TRY(cudaEventRecord(p->ev_k[c], stream));
+    CUDA_TRY(cudaStreamWaitEvent(p->s_out, p->ev_k[c], 0));
+    CUDA_TRY(cudaMemcpyAsync(h_out + ch.begin, p->d_host_out + ch.begin, n * 4, cudaMemcpyDeviceToHost, p->s_out));
+  }
+  CUDA_TRY(cudaEventRecord(p->ev_done, p->s_out));
+  CUDA_TRY(cudaStreamWaitEvent(stream, p->ev_done, 0));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  return ADJ_OK;
+}
+
+
+}  // namespace
 
 extern "C" {
 
@@ -1013,6 +1158,12 @@ int adj_plan_info(const adj_plan_t* p, adj_plan_info_t* info) {
 void adj_plan_destroy(adj_plan_t* p) {
   if (!p) return;
   free_blocks(p);
+  for (cudaEvent_t e : p->ev_in) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_k) cudaEventDestroy(e);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->ev_done) cudaEventDestroy(p->ev_done);
+  if (p->s_in) cudaStreamDestroy(p->s_in);
+  if (p->s_out) cudaStreamDestroy(p->s_out);
   cudaFree(p->d_tfs);
   cudaFree(p->d_params);
   cudaFree(p->d_sched);

@@ -372,16 +372,7 @@ __device__ __forceinline__ unsigned sm_id() {
   return r;
 }
 
-// Completes a claim whose atomicAdd on s->pos[range] returned k (issued earlier, so its
-// latency overlapped other work): the tile index, or the result of a full search when
-// the range turned out to be exhausted.
 static __device__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges, int& range);
-__device__ __forceinline__ int claim_resolve(SchedState* s, const unsigned* __restrict__ begin, int n_ranges,
-                                             int& range, unsigned k) {
-  const unsigned t = __ldg(begin + range) + k;
-  if (t < __ldg(begin + range + 1)) return (int)t;
-  return grab_tile(s, begin, n_ranges, range);
-}
 
 // First range after `from` (cyclically) whose bit is clear in the bitmap snapshot, or -1.
 __device__ __forceinline__ int next_open_range(const unsigned* ex, int from, int n_ranges) {
@@ -424,5 +415,25 @@ static __device__ __noinline__ int grab_tile(SchedState* s, const unsigned* __re
   }
   return -1;
 }
+
+// Thread 0's side of the tile claims: the range it takes tiles from, that range's bounds,
+// and one claim in flight (an atomicAdd issued one pipeline iteration before its result is
+// read, so its latency is hidden).
+struct Claimer {
+  int range = -1;
+  unsigned b0 = 0, b1 = 0;  // tiles [b0, b1) of `range`
+  unsigned k = 0;           // result of the claim in flight
+  __device__ __forceinline__ int grab(SchedState* s, const unsigned* __restrict__ begin, int n_ranges) {
+    const int t = grab_tile(s, begin, n_ranges, range);
+    b0 = __ldg(begin + range);
+    b1 = __ldg(begin + range + 1);
+    return t;
+  }
+  __device__ __forceinline__ void issue(SchedState* s) { k = atomicAdd(&s->pos[range], 1u); }
+  __device__ __forceinline__ int resolve(SchedState* s, const unsigned* __restrict__ begin, int n_ranges) {
+    if (b0 + k < b1) return (int)(b0 + k);
+    return grab(s, begin, n_ranges);
+  }
+};
 
 }  // namespace adjtx

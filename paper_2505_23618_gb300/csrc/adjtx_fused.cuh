@@ -329,16 +329,16 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
   __shared__ __align__(16) TileDev sDesc[4];
   __shared__ int sIdx[3];
   const int tid = threadIdx.x;
-  int range = -1;        // thread 0 only: the range claims come from
-  unsigned claim_k = 0;  // thread 0 only: pending claim
+  Claimer cl;  // used by thread 0 only
   auto list_bytes = [](const TileDev& d) { return (((d.blk_begin & 3) + d.nblk + 3) / 4) * 16; };
 
-  // Prologue: claim three tiles; fetch the records of tile 0, stage it, and start fetching
-  // the offsets of tile 1 and the descriptor of tile 2.
+  // Prologue: claim three tiles and put a claim for a fourth in flight; fetch the records
+  // of tile 0, stage it, and start fetching the offsets of tile 1 and the descriptor of tile 2.
   if (tid == 0) {
-    sIdx[0] = grab_tile(a.sched, a.range_begin, a.n_ranges, range);
-    sIdx[1] = sIdx[0] >= 0 ? grab_tile(a.sched, a.range_begin, a.n_ranges, range) : -1;
-    sIdx[2] = sIdx[1] >= 0 ? grab_tile(a.sched, a.range_begin, a.n_ranges, range) : -1;
+    sIdx[0] = cl.grab(a.sched, a.range_begin, a.n_ranges);
+    sIdx[1] = sIdx[0] >= 0 ? cl.grab(a.sched, a.range_begin, a.n_ranges) : -1;
+    sIdx[2] = sIdx[1] >= 0 ? cl.grab(a.sched, a.range_begin, a.n_ranges) : -1;
+    if (sIdx[2] >= 0) cl.issue(a.sched);
   }
   __syncthreads();
   int t = sIdx[0], tn = sIdx[1], tn2 = sIdx[2];
@@ -366,9 +366,9 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
 
   // Per tile k: (1) wait for everything fetched during the previous iteration, barrier;
   // (2) start copying tile k+1 into the other buffer, with its records, and the offsets of
-  // tile k+2; claim tile k+3; (3) row pass; (4) thread 0 resolves the claim and fetches that
-  // tile's descriptor; barrier; (5) column pass.  The copies of tile k+1 overlap both passes
-  // of tile k.
+  // tile k+2; thread 0 reads the claim issued an iteration ago (tile k+3), fetches that
+  // tile's descriptor and issues the claim of tile k+4; (3) row pass; (4) barrier;
+  // (5) column pass.  The copies of tile k+1 overlap both passes of tile k.
   for (int k = 0; t >= 0; ++k) {
     const int cur = k & 1;
     float* buf = reinterpret_cast<float*>(smem + cur * kBufBytes);
@@ -389,8 +389,16 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
       const TileDev dn2 = sDesc[(k + 2) & 3];
       copy_async<THREADS>(sOff[(k + 2) % 3], a.tile_blk + (dn2.blk_begin & ~3u), list_bytes(dn2));
     }
+    // sIdx[0] is free: every thread read it after the previous iteration's barrier (4)
+    if (tid == 0) {
+      const int t3 = tn2 >= 0 ? cl.resolve(a.sched, a.range_begin, a.n_ranges) : -1;
+      sIdx[0] = t3;
+      if (t3 >= 0) {
+        cp_async16(&sDesc[(k + 3) & 3], a.tiles + t3);
+        cl.issue(a.sched);
+      }
+    }
     cp_async_commit();
-    if (tid == 0 && tn2 >= 0) claim_k = atomicAdd(&a.sched->pos[range], 1u);
 
     // (3) row pass (horizontal transform, length w), in place
     const int w = td.w, h = td.h, nb = td.nblk;
@@ -405,13 +413,7 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
         default: row_pass<64, INV, THREADS>(tf, a.params, buf, nb, h); break;
       }
     }
-    // (4) sIdx[0] is free: every thread read it after the previous iteration's barrier (4)
-    if (tid == 0) {
-      const int t3 = tn2 >= 0 ? claim_resolve(a.sched, a.range_begin, a.n_ranges, range, claim_k) : -1;
-      sIdx[0] = t3;
-      if (t3 >= 0) cp_async16(&sDesc[(k + 3) & 3], a.tiles + t3);
-      cp_async_commit();
-    }
+    // (4)
     __syncthreads();
     const int tn3 = sIdx[0];
     // (5) column pass (vertical transform, length h), stores to global memory
