@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--frames", type=int, default=8, help="frames of the workload (profiling uses fewer)")
     p.add_argument("--no-multiple", action="store_true", help="skip the Multiple-forward measurement")
+    p.add_argument("--config5", dest="config5", action="store_true", default=True,
+                   help="measure the large-frame workload (default)")
+    p.add_argument("--no-config5", dest="config5", action="store_false")
     return p.parse_args()
 
 
@@ -284,6 +287,93 @@ def bench_multiple(args, rank, dev, stream, flush, peak):
                    f"{reps} L2-flushed repeats"}
 
 
+FITTED = os.path.join(ROOT, "paper_2505_23618_gb300", "params", "fitted.json")
+
+
+def config5_tfs():
+    """The large-frame workload's transforms: fitted DST-7 / DCT-8 approximations when the
+    fitted parameter file is present (horizontal DST-3 + 12-layer band; vertical DCT-2 + post
+    with the DCT-8 block S Q S of Eq. 5), else None (the workload's seeded parameters)."""
+    import numpy as np
+    import synth
+    try:
+        with open(FITTED) as f:
+            fit = json.load(f)
+        b = fit["band_dst3_64"]
+        h_tf = synth.Tf(n=64, core=synth.CORE_DST3, kind=synth.KIND_BAND,
+                        parities=np.array(b["parities"], np.uint8), angles=np.array(b["angles"]))
+        v_tfs = {n: synth.Tf(n=n, core=synth.CORE_DCT2, kind=synth.KIND_POST,
+                             q=np.array(fit[f"post_dct2_{n}"]["q_dct8"]))
+                 for n in (64, 32)}
+        return h_tf, v_tfs, "fitted (paper_2505_23618_gb300/params/fitted.json)"
+    except (OSError, KeyError, ValueError):
+        return None, None, "seeded"
+
+
+def bench_config5(args, rank, dev, stream, flush, peak):
+    """Large-frame workload (16 frames of 7680x4320, 64x64 and 64x32 blocks; horizontal
+    DST-7 approximation, vertical DCT-8 approximation): fused forward + inverse, and the exact
+    dense DST-7 / DCT-8 product on the same blocks as context.  Median of L2-flushed repeats."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2505_23618_gb300 as adj
+    from paper_2505_23618_gb300 import targets
+
+    h_tf, v_tfs, src = config5_tfs()
+    wl = synth.config5(seed=5 + 1000 * rank, h_tf=h_tf, v_tfs=v_tfs)
+    coefs, nb = wl.total, int(wl.blocks.size)
+    reps = max(3, min(args.steps, 10))
+    x = torch.from_numpy(wl.data).to(dev)
+    y = torch.empty(coefs, dtype=torch.float32, device=dev)
+    xr = torch.empty(coefs, dtype=torch.float32, device=dev)
+
+    def timed(fwd, inv):
+        for _ in range(2):
+            fwd()
+            inv()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+        for e in ev:
+            flush.fill_(6.0)
+            e[0].record(stream)
+            fwd()
+            e[1].record(stream)
+            flush.fill_(7.0)
+            e[2].record(stream)
+            inv()
+            e[3].record(stream)
+        torch.cuda.synchronize()
+        tf = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        ti = float(np.median([e[2].elapsed_time(e[3]) for e in ev]))
+        return tf, ti
+
+    out = {"workload": wl.name, "params": src}
+    with adj.Plan(wl.tfs) as plan:
+        plan.set_blocks(wl.blocks, coefs)
+        tiles = plan.info()["n_tiles"]
+        tf, ti = timed(lambda: plan.fwd(x, y, stream), lambda: plan.inv(y, xr, stream))
+        torch.cuda.synchronize()
+        rt = float((xr - x.float()).abs().max())
+    meta = tiles * 16 + nb * 4
+    bf, bi = coefs * 6 + meta, coefs * 8 + meta
+    out.update({"value": round(coefs / ((tf + ti) * 1e-3) / 1e9, 3), "unit": UNIT, "coefs": coefs,
+                "fwd_ms": round(tf, 4), "inv_ms": round(ti, 4),
+                "fwd_frac": round(bf / (tf * 1e-3) / 1e9 / peak, 4), "inv_frac": round(bi / (ti * 1e-3) / 1e9 / peak, 4),
+                "roundtrip_max_abs_err": rt})
+    # the exact transforms the adjustments stand in for, as dense products (Eq. 3)
+    dense = [targets.dense_tf(targets.dst7(64)), targets.dense_tf(targets.dct8(64)), targets.dense_tf(targets.dct8(32))]
+    with adj.Plan(dense) as plan:
+        plan.set_blocks(wl.blocks, coefs)
+        tf, ti = timed(lambda: plan.fwd(x, y, stream), lambda: plan.inv(y, xr, stream))
+    out["dense_dst7_dct8"] = {"value": round(coefs / ((tf + ti) * 1e-3) / 1e9, 3), "unit": UNIT,
+                              "fwd_ms": round(tf, 4), "inv_ms": round(ti, 4)}
+    out["vs_dense"] = round(out["value"] / out["dense_dst7_dct8"]["value"], 3)
+    out["how"] = f"median of {reps} L2-flushed repeats per kernel"
+    del x, y, xr
+    return out
+
+
 def run_fused(args):
     import numpy as np
     import torch
@@ -377,6 +467,7 @@ def run_fused(args):
 
     peak, peak_src = measured_peak()
     multiple = bench_multiple(args, rank, dev, stream, flush, peak) if not args.no_multiple else None
+    config5 = bench_config5(args, rank, dev, stream, flush, peak) if args.config5 else None
 
     # end to end through the host-buffer C-ABI calls (pinned memory), copies included
     h_x = torch.from_numpy(wl.data).pin_memory()
@@ -427,6 +518,7 @@ def run_fused(args):
                       "roundtrip_max_abs_err": plain_rt},
             "roofline": roof,
             "multiple": multiple,
+            "config5": config5,
             "kernels": {k: {"ms": round(v["ms"], 4), "GB/s": round(v["gbs"], 1), "frac": round(v["frac"], 4)}
                         for k, v in kern.items()},
             "clocks": clk.summary(),

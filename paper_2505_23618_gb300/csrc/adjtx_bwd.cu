@@ -142,7 +142,7 @@ __device__ void bwd_row(const TfDev& tf, const float* P, const float* bufU, floa
                         int nb, int h, const uint32_t* offs, float* gx) {
   constexpr int SH = sw_shift(W), MK = sw_mask(W);
   const int k = m_side(tf);
-  const int lgh = ilog2(h);
+  const int lgh = lg2(h);
   for (int l = threadIdx.x; l < nb * h; l += kBT) {
     const int b = l >> lgh, r = l & (h - 1);
     RowSw rowU{const_cast<float*>(bufU) + l * W, (r >> SH) & MK};

@@ -17,6 +17,9 @@ namespace adjtx {
 // packed line pair come from duplicated tables ({c, c, s, s} per rotation, {q, q} per Q
 // entry) so that they load as ready-made pairs.
 // ---------------------------------------------------------------------------------
+// log2 of a power of two at run time (one instruction instead of a loop).
+__device__ __forceinline__ int lg2(int x) { return 31 - __clz(x); }
+
 __device__ __forceinline__ float vmulv(float a, float b) { return a * b; }
 __device__ __forceinline__ float2 vmulv(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
@@ -268,6 +271,43 @@ struct ColSw {
   }
 };
 
+// Columns c and c + 1 (c even) of a W wide block in a swizzled tile buffer, as one line of
+// float2 elements: both sit in the same 16-byte chunk of every row, so each element pair is
+// one 8-byte shared load.
+template <int W>
+struct ColSw2 {
+  static constexpr int SH = sw_shift(W), MK = sw_mask(W), NK = MK + 1;
+  const float* p[NK];
+  const float* blk;
+  int c;
+  __device__ __forceinline__ ColSw2(const float* block, int col) : blk(block), c(col) {
+#pragma unroll
+    for (int k = 0; k < NK; ++k) p[k] = block + ((((col >> 2) ^ k)) << 2) + (col & 3);
+  }
+  template <int N>
+  __device__ __forceinline__ void load(float2 (&v)[N]) const {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = *reinterpret_cast<const float2*>(p[(i >> SH) & MK] + i * W);
+  }
+  __device__ __forceinline__ float2 get_rt(int i) const {
+    return *reinterpret_cast<const float2*>(blk + i * W + ((((c >> 2) ^ ((i >> SH) & MK))) << 2) + (c & 3));
+  }
+};
+
+// Columns c and c + 1 (c even) of an output block in global memory: 8-byte stores, element i
+// at p + i * S.
+template <int S>
+struct DstGCol2 {
+  float* p;
+  __device__ __forceinline__ void put(int i, float2 x) const { *reinterpret_cast<float2*>(p + i * S) = x; }
+  __device__ __forceinline__ void put_rt(int i, float2 x) const { *reinterpret_cast<float2*>(p + i * S) = x; }
+  template <int N>
+  __device__ __forceinline__ void store(const float2 (&v)[N]) const {
+#pragma unroll
+    for (int i = 0; i < N; ++i) *reinterpret_cast<float2*>(p + i * S) = v[i];
+  }
+};
+
 // A column of an output block in global memory (element i at p[i * S]).
 template <int S>
 struct DstGCol {
@@ -372,67 +412,74 @@ __device__ __forceinline__ unsigned sm_id() {
   return r;
 }
 
-static __device__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges, int& range);
-
-// First range after `from` (cyclically) whose bit is clear in the bitmap snapshot, or -1.
-__device__ __forceinline__ int next_open_range(const unsigned* ex, int from, int n_ranges) {
-  for (int step = 1; step <= n_ranges; ++step) {
-    const int r = (from + step) % n_ranges;
-    if (!((ex[r >> 5] >> (r & 31)) & 1u)) return r;
-  }
-  return -1;
-}
-
-// Next tile for this CTA (called by one thread), or -1 when every tile is claimed.
-// `range` is the CTA's current range (initially -1: start at the SM's own range).
-// Every probe either returns a tile or marks one more range exhausted, so the loop ends
-// after at most 2 * n_ranges + 2 probes.
-static __device__ __noinline__ int grab_tile(SchedState* s, const unsigned* __restrict__ begin, int n_ranges,
-                                       int& range) {
-  if (range < 0) range = (int)(sm_id() % (unsigned)n_ranges);
-  unsigned ex[kMaxRanges / 32];
-  bool have = false;
-  for (int probes = 0; probes < 2 * n_ranges + 2; ++probes) {
-    const unsigned k = atomicAdd(&s->pos[range], 1u);
-    const unsigned t = __ldg(begin + range) + k;
-    if (t < __ldg(begin + range + 1)) return (int)t;
-    atomicOr(&s->exhausted[range >> 5], 1u << (range & 31));
-    if (!have) {
-      const volatile unsigned* g = s->exhausted;
-      for (int i = 0; i < (n_ranges + 31) / 32; ++i) ex[i] = g[i];
-      have = true;
-    }
-    ex[range >> 5] |= 1u << (range & 31);
-    int next = next_open_range(ex, range, n_ranges);
-    if (next < 0) {
-      // the snapshot says everything is taken: confirm with a fresh one
-      const volatile unsigned* g = s->exhausted;
-      for (int i = 0; i < (n_ranges + 31) / 32; ++i) ex[i] = g[i];
-      next = next_open_range(ex, range, n_ranges);
-      if (next < 0) return -1;
-    }
-    range = next;
-  }
-  return -1;
-}
-
-// Thread 0's side of the tile claims: the range it takes tiles from, that range's bounds,
-// and one claim in flight (an atomicAdd issued one pipeline iteration before its result is
-// read, so its latency is hidden).
+// Tile claims, made by warp 0 of a CTA for the whole CTA.  A CTA starts on the range of
+// its SM and claims tiles from it with one atomicAdd each; the claim for a tile is issued
+// one pipeline iteration before its result is read (lane 0 holds it meanwhile), so its
+// latency is hidden.  When the range is used up, the warp reads every range's counter at
+// once (each lane a few ranges), moves to the range with the most unclaimed tiles and
+// claims there.  A failed claim means that range's tiles were all taken by other CTAs, so
+// it drops out of later searches: the search ends after at most n_ranges failures.
 struct Claimer {
   int range = -1;
   unsigned b0 = 0, b1 = 0;  // tiles [b0, b1) of `range`
-  unsigned k = 0;           // result of the claim in flight
-  __device__ __forceinline__ int grab(SchedState* s, const unsigned* __restrict__ begin, int n_ranges) {
-    const int t = grab_tile(s, begin, n_ranges, range);
-    b0 = __ldg(begin + range);
-    b1 = __ldg(begin + range + 1);
-    return t;
+  unsigned k = 0;           // lane 0: result of the claim in flight
+
+  __device__ __forceinline__ void set_range(const unsigned* __restrict__ begin, int r) {
+    range = r;
+    b0 = __ldg(begin + r);
+    b1 = __ldg(begin + r + 1);
   }
-  __device__ __forceinline__ void issue(SchedState* s) { k = atomicAdd(&s->pos[range], 1u); }
+  // One claim on `range`, waited for (all lanes of warp 0; uniform result).
+  __device__ __forceinline__ unsigned claim_now(SchedState* s) {
+    unsigned v = 0;
+    if ((threadIdx.x & 31) == 0) v = atomicAdd(&s->pos[range], 1u);
+    return __shfl_sync(0xffffffffu, v, 0);
+  }
+  // Next tile (all lanes of warp 0), or -1 when every tile has been claimed.  The current
+  // range is tried first unless the caller already knows it is used up.
+  __device__ __noinline__ int grab(SchedState* s, const unsigned* __restrict__ begin, int n_ranges,
+                                  bool try_current = true) {
+    const int lane = threadIdx.x & 31;
+    if (range < 0) set_range(begin, (int)(sm_id() % (unsigned)n_ranges));
+    if (try_current) {
+      const unsigned c = claim_now(s);
+      if (b0 + c < b1) return (int)(b0 + c);
+    }
+    for (int guard = 0; guard <= n_ranges + 1; ++guard) {
+      int best = -1, best_left = 0;
+      for (int r = lane; r < n_ranges; r += 32) {
+        const int size = (int)(__ldg(begin + r + 1) - __ldg(begin + r));
+        const int left = size - (int)*reinterpret_cast<volatile unsigned*>(&s->pos[r]);
+        if (left > best_left) {
+          best_left = left;
+          best = r;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const int l2 = __shfl_xor_sync(0xffffffffu, best_left, o);
+        const int r2 = __shfl_xor_sync(0xffffffffu, best, o);
+        if (l2 > best_left || (l2 == best_left && r2 > best)) {
+          best_left = l2;
+          best = r2;
+        }
+      }
+      if (best < 0) return -1;
+      set_range(begin, best);
+      const unsigned c = claim_now(s);
+      if (b0 + c < b1) return (int)(b0 + c);
+    }
+    return -1;
+  }
+  // Lane 0 issues the next claim on the current range; its result is read by resolve().
+  __device__ __forceinline__ void issue(SchedState* s) {
+    if ((threadIdx.x & 31) == 0) k = atomicAdd(&s->pos[range], 1u);
+  }
+  // All lanes of warp 0: the tile of the claim issued earlier (searching if it failed).
   __device__ __forceinline__ int resolve(SchedState* s, const unsigned* __restrict__ begin, int n_ranges) {
-    if (b0 + k < b1) return (int)(b0 + k);
-    return grab(s, begin, n_ranges);
+    const unsigned c = __shfl_sync(0xffffffffu, k, 0);
+    if (b0 + c < b1) return (int)(b0 + c);
+    return grab(s, begin, n_ranges, false);
   }
 };
 

@@ -25,43 +25,53 @@
 
 namespace adjtx {
 
-// Issue the asynchronous copies of one tile's input into a tile buffer.
-template <bool INV, int THREADS>
-__device__ __forceinline__ void stage_tile(const TileDev& td, const uint32_t* sOff, const void* in, float* buf) {
-  const int w = td.w, h = td.h, nb = td.nblk;
-  const int sh = sw_shift(w), mk = sw_mask(w);
+// Issue the asynchronous copies of one tile's input into a tile buffer (block width W).
+template <int W, bool INV, int THREADS>
+__device__ __forceinline__ void stage_tile_w(const TileDev& td, const uint32_t* sOff, const void* in, float* buf) {
+  constexpr int SH = sw_shift(W), MK = sw_mask(W);
+  const int h = td.h, nb = td.nblk, lgh = lg2(h);
   if constexpr (INV) {
-    // FP32 chunks of 4 samples: w/4 per row
-    const int lg_cpr = ilog2(w >> 2), lg_cpb = ilog2((w * h) >> 2);
-    const int total = nb << lg_cpb;
+    // FP32 chunks of 4 samples: W/4 per row
+    constexpr int LG_CPR = ilog2(W / 4);
+    const int lg_cpb = LG_CPR + lgh, total = nb << lg_cpb;
     const float* src = static_cast<const float*>(in);
     for (int g = threadIdx.x; g < total; g += THREADS) {
       const int b = g >> lg_cpb, gg = g & ((1 << lg_cpb) - 1);
-      const int r = gg >> lg_cpr, q = gg & ((1 << lg_cpr) - 1);
+      const int r = gg >> LG_CPR, q = gg & ((1 << LG_CPR) - 1);
       const size_t off = (size_t)sOff[b] * 16;
-      cp_async16(buf + b * w * h + r * w + ((q ^ ((r >> sh) & mk)) << 2), src + off + gg * 4);
+      cp_async16(buf + (b << (lgh + ilog2(W))) + r * W + ((q ^ ((r >> SH) & MK)) << 2), src + off + gg * 4);
     }
-  } else if (w >= 8) {
-    // int16 chunks of 8 samples: w/8 per row, placed at FP32 chunk slot q ^ f(r)
-    const int lg_cpr = ilog2(w >> 3), lg_cpb = ilog2((w * h) >> 3);
-    const int total = nb << lg_cpb;
+  } else if constexpr (W >= 8) {
+    // int16 chunks of 8 samples: W/8 per row, placed at FP32 chunk slot q ^ f(r)
+    constexpr int LG_CPR = ilog2(W / 8);
+    const int lg_cpb = LG_CPR + lgh, total = nb << lg_cpb;
     const int16_t* src = static_cast<const int16_t*>(in);
     for (int g = threadIdx.x; g < total; g += THREADS) {
       const int b = g >> lg_cpb, gg = g & ((1 << lg_cpb) - 1);
-      const int r = gg >> lg_cpr, q = gg & ((1 << lg_cpr) - 1);
+      const int r = gg >> LG_CPR, q = gg & ((1 << LG_CPR) - 1);
       const size_t off = (size_t)sOff[b] * 16;
-      cp_async16(buf + b * w * h + r * w + ((q ^ ((r >> sh) & mk)) << 2), src + off + gg * 8);
+      cp_async16(buf + (b << (lgh + ilog2(W))) + r * W + ((q ^ ((r >> SH) & MK)) << 2), src + off + gg * 8);
     }
   } else {
-    // w = 4: one int16 row is 8 bytes, copied to the start of its 16-byte row region
+    // W = 4: one int16 row is 8 bytes, copied to the start of its 16-byte row region
     const int total = nb * h;
     const int16_t* src = static_cast<const int16_t*>(in);
-    const int lgh = ilog2(h);
     for (int g = threadIdx.x; g < total; g += THREADS) {
       const int b = g >> lgh, r = g & (h - 1);
       const size_t off = (size_t)sOff[b] * 16;
       cp_async8(buf + b * 4 * h + r * 4, src + off + r * 4);
     }
+  }
+}
+
+template <bool INV, int THREADS>
+__device__ __forceinline__ void stage_tile(const TileDev& td, const uint32_t* sOff, const void* in, float* buf) {
+  switch (td.w) {
+    case 4: stage_tile_w<4, INV, THREADS>(td, sOff, in, buf); break;
+    case 8: stage_tile_w<8, INV, THREADS>(td, sOff, in, buf); break;
+    case 16: stage_tile_w<16, INV, THREADS>(td, sOff, in, buf); break;
+    case 32: stage_tile_w<32, INV, THREADS>(td, sOff, in, buf); break;
+    default: stage_tile_w<64, INV, THREADS>(td, sOff, in, buf); break;
   }
 }
 
@@ -329,16 +339,21 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
   __shared__ __align__(16) TileDev sDesc[4];
   __shared__ int sIdx[3];
   const int tid = threadIdx.x;
-  Claimer cl;  // used by thread 0 only
+  Claimer cl;  // used by warp 0 only
   auto list_bytes = [](const TileDev& d) { return (((d.blk_begin & 3) + d.nblk + 3) / 4) * 16; };
 
-  // Prologue: claim three tiles and put a claim for a fourth in flight; fetch the records
+  // Prologue: warp 0 claims three tiles and puts a claim for a fourth in flight; fetch the records
   // of tile 0, stage it, and start fetching the offsets of tile 1 and the descriptor of tile 2.
-  if (tid == 0) {
-    sIdx[0] = cl.grab(a.sched, a.range_begin, a.n_ranges);
-    sIdx[1] = sIdx[0] >= 0 ? cl.grab(a.sched, a.range_begin, a.n_ranges) : -1;
-    sIdx[2] = sIdx[1] >= 0 ? cl.grab(a.sched, a.range_begin, a.n_ranges) : -1;
-    if (sIdx[2] >= 0) cl.issue(a.sched);
+  if (tid < 32) {
+    const int t0 = cl.grab(a.sched, a.range_begin, a.n_ranges);
+    const int t1 = t0 >= 0 ? cl.grab(a.sched, a.range_begin, a.n_ranges) : -1;
+    const int t2 = t1 >= 0 ? cl.grab(a.sched, a.range_begin, a.n_ranges) : -1;
+    if (t2 >= 0) cl.issue(a.sched);
+    if (tid == 0) {
+      sIdx[0] = t0;
+      sIdx[1] = t1;
+      sIdx[2] = t2;
+    }
   }
   __syncthreads();
   int t = sIdx[0], tn = sIdx[1], tn2 = sIdx[2];
@@ -366,7 +381,7 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
 
   // Per tile k: (1) wait for everything fetched during the previous iteration, barrier;
   // (2) start copying tile k+1 into the other buffer, with its records, and the offsets of
-  // tile k+2; thread 0 reads the claim issued an iteration ago (tile k+3), fetches that
+  // tile k+2; warp 0 reads the claim issued an iteration ago (tile k+3), fetches that
   // tile's descriptor and issues the claim of tile k+4; (3) row pass; (4) barrier;
   // (5) column pass.  The copies of tile k+1 overlap both passes of tile k.
   for (int k = 0; t >= 0; ++k) {
@@ -390,12 +405,12 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
       copy_async<THREADS>(sOff[(k + 2) % 3], a.tile_blk + (dn2.blk_begin & ~3u), list_bytes(dn2));
     }
     // sIdx[0] is free: every thread read it after the previous iteration's barrier (4)
-    if (tid == 0) {
+    if (tid < 32) {
       const int t3 = tn2 >= 0 ? cl.resolve(a.sched, a.range_begin, a.n_ranges) : -1;
-      sIdx[0] = t3;
-      if (t3 >= 0) {
-        cp_async16(&sDesc[(k + 3) & 3], a.tiles + t3);
-        cl.issue(a.sched);
+      if (t3 >= 0) cl.issue(a.sched);
+      if (tid == 0) {
+        sIdx[0] = t3;
+        if (t3 >= 0) cp_async16(&sDesc[(k + 3) & 3], a.tiles + t3);
       }
     }
     cp_async_commit();
@@ -453,7 +468,6 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
   __syncthreads();
   if (sLast) {
     for (int i = tid; i < kMaxRanges; i += THREADS) a.sched->pos[i] = 0u;
-    for (int i = tid; i < kMaxRanges / 32; i += THREADS) a.sched->exhausted[i] = 0u;
     if (tid == 0) a.sched->done = 0u;
     __threadfence();
   }

@@ -50,19 +50,17 @@ constexpr int kSmemBytes = 2 * kBufBytes;
 constexpr int kMaxTileBlocks = 256;
 
 // Work distribution.  The tile list is sorted by class, so consecutive tiles share
-// (w, h, core, adjustment) and therefore code.  The planner cuts the list into kRanges
-// contiguous ranges of about equal work; the CTAs of SM s take tiles from range
+// (w, h, core, adjustment) and therefore code.  The planner cuts the list into up to
+// kMaxRanges contiguous ranges of about equal work; the CTAs of SM s take tiles from range
 // s mod n_ranges in order, so each SM walks through neighbouring classes and keeps its
-// instruction cache warm.  A CTA whose range is empty marks it in the exhausted bitmap
-// and moves on to the next range that is not marked (work stealing); the bitmap keeps
-// that search O(1) per range.  All words are zero between launches (the last CTA of a
+// instruction cache warm.  A CTA whose range is used up moves to the range with the most
+// unclaimed tiles (work stealing).  All words are zero between launches (the last CTA of a
 // launch clears them).
 constexpr int kMaxRanges = 256;
 struct SchedState {
-  unsigned pos[kMaxRanges];        // tiles taken from each range
-  unsigned exhausted[kMaxRanges / 32];
+  unsigned pos[kMaxRanges];        // claims made on each range (tiles taken, plus failed claims)
   unsigned done;                   // CTAs finished
-  unsigned pad[7];
+  unsigned pad[15];
 };
 
 ADJ_HD int ilog2(int x) {

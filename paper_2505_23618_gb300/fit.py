@@ -302,3 +302,102 @@ class Fitter:
 
     def close(self):
         self.plan.close()
+
+
+# ---------------------------------------------------------------------------------------
+# The fits of the design step: the DST-7 approximations of the fitting workload (65536
+# AR(1) 64x64 blocks, rho 0.95, M = 16) for both parameterisations, and the pairings the
+# large-frame workload runs (DST-3 + band; DCT-2 + post at 64 and 32 points, whose DCT-8
+# counterpart follows by Eq. 5).
+# ---------------------------------------------------------------------------------------
+
+FITS = {
+    "band_dct2_64": dict(n=64, core=0, kind=1, parities=(0, 1) * 6),
+    "post_dst2_64": dict(n=64, core=2, kind=2, k=32),
+    "band_dst3_64": dict(n=64, core=3, kind=1, parities=(0, 1) * 6),
+    "post_dct2_64": dict(n=64, core=0, kind=2, k=32),
+    "post_dct2_32": dict(n=32, core=0, kind=2, k=16),
+}
+
+
+def _proxy_of(fitter, tf):
+    """Coding-gain proxy of the fitter's blocks under another 1-D transform `tf`."""
+    torch = fitter.torch
+    with _lib.Plan([tf]) as plan:
+        blocks = np.zeros(fitter.nb, dtype=_lib.BLOCK_DTYPE)
+        n = fitter.cfg.n
+        blocks["offset"] = np.arange(fitter.nb, dtype=np.int64) * n * n
+        blocks["w"] = blocks["h"] = n
+        plan.set_blocks(blocks, fitter.nb * n * n)
+        stream = torch.cuda.current_stream(fitter.dev)
+        plan.fwd(fitter.x, fitter.y, stream)
+        _lib.check(plan._lib.adj_coding_gain_proxy(fitter.y.data_ptr(), fitter.nb, n * n, fitter.work.data_ptr(),
+                                                   fitter.loss_dev.data_ptr(), None, stream.cuda_stream))
+        torch.cuda.synchronize(fitter.dev)
+        return float(fitter.loss_dev.item())
+
+
+def run_fit(name, steps, lr=0.01, log_every=0):
+    """Runs one named fit; returns its record (parameters, history summary, metrics)."""
+    cfg = FitConfig(**FITS[name], steps=steps, lr=lr)
+    f = Fitter(cfg)
+    n, m = cfg.n, cfg.m
+    loss0, basis0, proxy0, _ = f.loss_and_grad()
+    f.run(steps, log_every=log_every)
+    loss1, basis1, proxy1, g1 = f.loss_and_grad()
+    H = f.H()
+    D = f.D
+    # coding gains relative to the DCT-2 on the same blocks: (10 / ln 10) (P_DCT2 - P_H)
+    p_dct2 = _proxy_of(f, {"n": n, "core": 0, "kind": 0})
+    p_core = _proxy_of(f, {"n": n, "core": cfg.core, "kind": 0})
+    p_dst7 = _proxy_of(f, targets.dense_tf(D))
+    db = 10.0 / math.log(10.0)
+    rec = {
+        "name": name,
+        "config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in FITS[name].items()},
+        "target": cfg.target, "m": m, "lam": cfg.lam, "blocks": cfg.blocks, "rho": cfg.rho, "sigma": cfg.sigma,
+        "seed": cfg.seed, "steps": steps, "lr": lr,
+        "start": {"loss": loss0, "basis": basis0, "proxy": proxy0},
+        "final": {"loss": loss1, "basis": basis1, "proxy": proxy1, "grad_norm": float(np.linalg.norm(g1)),
+                  "max_abs_basis_dev_first_m": float(np.abs(H[:m] - D[:m]).max())},
+        "coding_gain_db_vs_dct2": {"fitted": db * (p_dct2 - proxy1), "core_alone": db * (p_dct2 - p_core),
+                                   "exact_dst7": db * (p_dct2 - p_dst7)},
+        "history": [cfg.history[i] for i in range(0, len(cfg.history), max(1, len(cfg.history) // 20))],
+    }
+    if cfg.kind == 1:
+        rec["parities"] = list(cfg.parities)
+        rec["angles"] = f.theta.tolist()
+    else:
+        rec["k"] = cfg.k
+        rec["q"] = f.q().tolist()
+        rec["q_dct8"] = targets.chessboard(f.q()).tolist()
+    f.close()
+    return rec
+
+
+def main(argv=None):
+    import argparse
+    import time
+    ap = argparse.ArgumentParser(description="Fit the DST-7 adjustments on the GPU and write them as JSON.")
+    ap.add_argument("--out", required=True, help="output JSON file")
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--lr", type=float, default=0.01)
+    ap.add_argument("--only", nargs="*", default=None, help="names of the fits to run (default: all)")
+    a = ap.parse_args(argv)
+    out = {}
+    for name in (a.only or list(FITS)):
+        t0 = time.time()
+        rec = run_fit(name, a.steps, a.lr)
+        rec["seconds"] = round(time.time() - t0, 2)
+        out[name] = rec
+        print(json.dumps({k: rec[k] for k in ("name", "start", "final", "coding_gain_db_vs_dct2", "seconds")}),
+              flush=True)
+    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    with open(a.out, "w") as fh:
+        json.dump(out, fh)
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+    sys.exit(main())
