@@ -227,7 +227,7 @@ int adj_transform_inv_plain(adj_plan_t* plan, const float* d_coef, float* d_resi
 /*
  * Host-buffer variants: copy the input from host memory to plan-owned device staging
  * buffers, transform, copy the result back and wait for it.  The block list (in storage
- * order) is cut into chunks of about 4 M samples (at most 16); each chunk's input copy,
+ * order) is cut into chunks of about 2 M samples (at most 32); each chunk's input copy,
  * kernel launch and output copy run on three streams, so the copies of one chunk overlap
  * the kernel and copies of the others.  Page-locked host memory gives full copy bandwidth.
  * Samples of h_out outside every block are left unchanged or set to zero.  The staging

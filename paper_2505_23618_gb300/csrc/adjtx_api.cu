@@ -54,8 +54,8 @@ struct TfHost {
 // Host-buffer path: the offset-sorted block list is cut into chunks of about
 // kHostChunkCoefs coefficients (at most kMaxHostChunks); chunk c's input copy, kernel and
 // output copy run on three streams, so copies of one chunk overlap the kernel of another.
-constexpr int64_t kHostChunkCoefs = 4 << 20;
-constexpr int kMaxHostChunks = 16;
+constexpr int64_t kHostChunkCoefs = 2 << 20;
+constexpr int kMaxHostChunks = 32;
 struct HostChunk {
   int64_t begin, end;   // samples [begin, end) covered by the chunk's blocks
   int tile0, n_tiles;   // the chunk's tiles in the host tile list

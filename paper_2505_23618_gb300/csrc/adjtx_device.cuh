@@ -137,9 +137,12 @@ __device__ __forceinline__ void post_fwd_k(const T (&v)[N], const TfDev& tf, con
   for (int i = KT; i < N; ++i) dst.put(i, v[i]);
 #pragma unroll 1
   for (int i = 0; i < KT; i += R) {
-    T acc[R];
+    // four partial sums per row (one per position in a Q quad): dependency chains of KT/4
+    T acc[R][4];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = vzero(v[0]);
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[r][e] = vzero(v[0]);
 #pragma unroll
     for (int g = 0; g < KT / 4; ++g) {
 #pragma unroll
@@ -147,11 +150,11 @@ __device__ __forceinline__ void post_fwd_k(const T (&v)[N], const TfDev& tf, con
         T q[4];
         q_quad(P, tf, i + r, g, q);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[r] = vfma(q[e], v[4 * g + e], acc[r]);
+        for (int e = 0; e < 4; ++e) acc[r][e] = vfma(q[e], v[4 * g + e], acc[r][e]);
       }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst.put_rt(i + r, acc[r]);
+    for (int r = 0; r < R; ++r) dst.put_rt(i + r, vadd(vadd(acc[r][0], acc[r][1]), vadd(acc[r][2], acc[r][3])));
   }
 }
 

@@ -104,12 +104,12 @@ __device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restric
   constexpr int lgw = ilog2(W);
   const int nlines = nb * W;
   if constexpr (H <= 32) {
-    const int half = nlines >> 1;
-    for (int l = threadIdx.x; l < half; l += THREADS) {
-      const int l2 = l + half;
-      const int b1 = l >> lgw, c1 = l & (W - 1), b2 = l2 >> lgw, c2 = l2 & (W - 1);
-      Pair<ColSw<W>> src{ColSw<W>(buf + b1 * (W * H), c1), ColSw<W>(buf + b2 * (W * H), c2)};
-      Pair<DstGCol<W>> dst{DstGCol<W>{out + (size_t)sOff[b1] * 16 + c1}, DstGCol<W>{out + (size_t)sOff[b2] * 16 + c2}};
+    // adjacent columns (c, c + 1) as one packed pair: 8-byte shared loads and global stores
+    const int pairs = nlines >> 1;
+    for (int l = threadIdx.x; l < pairs; l += THREADS) {
+      const int b = (2 * l) >> lgw, c = (2 * l) & (W - 1);
+      const ColSw2<W> src(buf + b * (W * H), c);
+      const DstGCol2<W> dst{out + (size_t)sOff[b] * 16 + c};
       line_transform<H, INV, false, float2>(tf, P, src, dst);
     }
   } else {
@@ -165,25 +165,26 @@ __device__ __forceinline__ void split_post_k(const float (&v)[N], const TfDev& t
   constexpr int R = PostRows<KT, float>::R;
 #pragma unroll 1
   for (int i = 0; i < k; i += R) {
-    float e[R], o[R];
+    float acc[R][4];  // by position in a Q quad: 0, 2 even columns, 1, 3 odd columns
 #pragma unroll
-    for (int r = 0; r < R; ++r) e[r] = o[r] = 0.f;
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int x = 0; x < 4; ++x) acc[r][x] = 0.f;
 #pragma unroll
     for (int g = 0; g < KT / 4; ++g) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float q[4];
         q_quad(P, tf, i + r, g, q);
-        e[r] = fmaf(q[0], v[4 * g], e[r]);
-        o[r] = fmaf(q[1], v[4 * g + 1], o[r]);
-        e[r] = fmaf(q[2], v[4 * g + 2], e[r]);
-        o[r] = fmaf(q[3], v[4 * g + 3], o[r]);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) acc[r][x] = fmaf(q[x], v[4 * g + x], acc[r][x]);
       }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int ii = i + r;
-      if (ii < k) emit(ii, e[r] + o[r], (ii & 1) ? o[r] - e[r] : e[r] - o[r]);
+      const float e = acc[r][0] + acc[r][2], o = acc[r][1] + acc[r][3];
+      if (ii < k) emit(ii, e + o, (ii & 1) ? o - e : e - o);
     }
   }
 }
