@@ -588,3 +588,54 @@ def multiple_blocks(x_flat, blocks, tfs):
 
 __all__ += ["MULTI_COMBOS", "post_c8_from_s7", "multiple_1d", "multiple_2d", "multiple_side_size",
             "multiple_side", "multiple_assemble", "multiple_blocks"]
+
+
+# --------------------------------------------------------------------------
+# Blocks inside a frame.  The adjusted transforms apply to W x B and B x H regions of a
+# frame (Section 2.2), so a codec holds its residual as a frame; the transform reads each
+# block from its position there, and the reconstruction goes back to the same position.
+# --------------------------------------------------------------------------
+
+FRAME_BLOCK_FIELDS = ("x", "y", "w", "h", "tf_h", "tf_v")
+
+
+def frame_coef_offsets(blocks) -> np.ndarray:
+    """Packed coefficient offsets of frame blocks: block i's coefficients follow those of
+    blocks 0..i-1 in list order, h x w row-major each."""
+    sz = np.asarray(blocks["w"], dtype=np.int64) * np.asarray(blocks["h"], dtype=np.int64)
+    return np.concatenate([[0], np.cumsum(sz)]).astype(np.int64)
+
+
+def forward_frame(frame, blocks, tfs) -> np.ndarray:
+    """Packed FP64 coefficients of the blocks of a 2-D residual frame (rows = frame lines)."""
+    frame = np.asarray(frame)
+    off = frame_coef_offsets(blocks)
+    out = np.zeros(int(off[-1]), dtype=np.float64)
+    mats = [tf_matrix(t) for t in tfs]
+    for i, b in enumerate(blocks):
+        x, y, w, h = int(b["x"]), int(b["y"]), int(b["w"]), int(b["h"])
+        X = frame[y:y + h, x:x + w].astype(np.float64)
+        out[off[i]:off[i + 1]] = forward_2d(X, mats[int(b["tf_h"])], mats[int(b["tf_v"])]).ravel()
+    return out
+
+
+def inverse_frame(coef, blocks, tfs, frame_shape, fill=0.0) -> np.ndarray:
+    """FP64 reconstruction frame of packed coefficients: every block's inverse placed at its
+    position; samples outside every block keep `fill`."""
+    coef = np.asarray(coef, dtype=np.float64)
+    off = frame_coef_offsets(blocks)
+    out = np.full(frame_shape, fill, dtype=np.float64)
+    mats = [tf_matrix(t) for t in tfs]
+    for i, b in enumerate(blocks):
+        x, y, w, h = int(b["x"]), int(b["y"]), int(b["w"]), int(b["h"])
+        Y = coef[off[i]:off[i + 1]].reshape(h, w)
+        out[y:y + h, x:x + w] = inverse_2d(Y, mats[int(b["tf_h"])], mats[int(b["tf_v"])])
+    return out
+
+
+def round_to_int16(x) -> np.ndarray:
+    """Round half to even and saturate to the int16 range."""
+    return np.clip(np.rint(np.asarray(x, dtype=np.float64)), -32768, 32767).astype(np.int16)
+
+
+__all__ += ["FRAME_BLOCK_FIELDS", "frame_coef_offsets", "forward_frame", "inverse_frame", "round_to_int16"]

@@ -87,3 +87,31 @@ def test_band_fit_reduces_loss():
     last = f.run(steps=40)
     assert last < first
     f.close()
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_eq2_fit(kind):
+    """The paper's criterion (Eq. 2): the fitter's term equals the oracle's weighted error of
+    the same H, its gradient agrees with central differences, and a short fit lowers it."""
+    f = _fitter(kind, lam=0.0, eq2=True, blocks=64)
+    rng = np.random.default_rng(10 + kind)
+    p0 = f.params() + rng.uniform(-0.05, 0.05, f.params().size)
+    f.set_params(p0)
+    loss, basis, _, g = f.loss_and_grad()
+    assert abs(basis - O.eq2_weighted_error(f.H(), O.dst7(32))) <= 1e-12 * max(1.0, basis)
+    assert loss == pytest.approx(basis, rel=1e-12)
+    sel = rng.choice(p0.size, min(8, p0.size), replace=False)
+    fd = []
+    for j in sel:
+        vals = []
+        for s in (1, -1):
+            p = p0.copy()
+            p[j] += s * 1e-5
+            f.set_params(p)
+            vals.append(f.loss_and_grad()[0])
+        fd.append((vals[0] - vals[1]) / 2e-5)
+    f.set_params(p0)
+    assert np.linalg.norm(g[sel] - np.array(fd)) / np.linalg.norm(fd) <= 1e-6
+    first = f.loss_and_grad()[0]
+    assert f.run(steps=30) < first
+    f.close()

@@ -332,3 +332,44 @@ def test_planted_mistakes():
 
     # 2-D transform with the horizontal / vertical roles swapped
     assert pin_orientation(lambda X, Hh, Hv: Hh @ X @ Hv.T, N_h=8, N_v=8) > 1e-3
+
+
+# --------------------------------------------------------------------------
+# blocks inside a frame
+# --------------------------------------------------------------------------
+
+def _frame_case(seed=0):
+    rng = np.random.default_rng(seed)
+    H, W = 48, 80
+    frame = rng.integers(-300, 300, (H, W)).astype(np.int16)
+    dt = np.dtype([("x", "<i4"), ("y", "<i4"), ("w", "<u2"), ("h", "<u2"), ("tf_h", "<u2"), ("tf_v", "<u2")])
+    tfs = [synth.Tf(n=n, core=int(rng.integers(0, 4))) for n in (4, 8, 16, 32)]
+    tfs += [synth.random_band(rng, 16, 3, [0, 1]), synth.random_post(rng, 32, 0, 8)]
+    idx = {4: 0, 8: 1, 16: 2, 32: 3}
+    rows = [(0, 0, 32, 16, 5, 2), (32, 0, 16, 16, 4, 4), (48, 4, 8, 8, 1, 1), (4, 16, 4, 32, 0, 3),
+            (12, 20, 16, 4, 2, 0), (40, 24, 32, 8, 3, 1)]
+    return frame, np.array(rows, dtype=dt), tfs
+
+
+def test_frame_blocks_match_packed_blocks():
+    """A frame block transforms exactly like the same samples packed on their own, and the
+    inverse puts every block back at its position (round trip exact in FP64)."""
+    frame, blocks, tfs = _frame_case()
+    coef = O.forward_frame(frame, blocks, tfs)
+    off = O.frame_coef_offsets(blocks)
+    for i, b in enumerate(blocks):
+        x, y, w, h = (int(b[f]) for f in ("x", "y", "w", "h"))
+        packed = np.zeros(1, dtype=synth.BLOCK_DTYPE)
+        packed[0] = (0, w, h, b["tf_h"], b["tf_v"])
+        ref = O.forward_blocks(frame[y:y + h, x:x + w].ravel(), packed, tfs)
+        assert np.array_equal(coef[off[i]:off[i + 1]], ref)
+    rec = O.inverse_frame(coef, blocks, tfs, frame.shape, fill=np.nan)
+    covered = ~np.isnan(rec)
+    assert covered.sum() == int(off[-1])            # blocks do not overlap
+    assert np.abs(rec[covered] - frame[covered]).max() < 1e-9
+    assert np.array_equal(O.round_to_int16(rec[covered]), frame[covered])
+
+
+def test_round_to_int16():
+    x = np.array([0.5, 1.5, -0.5, -1.5, 2.4999, 40000.0, -40000.0, -2.5])
+    assert list(O.round_to_int16(x)) == [0, 2, 0, -2, 2, 32767, -32768, -2]
