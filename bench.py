@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--config5", dest="config5", action="store_true", default=True,
                    help="measure the large-frame workload (default)")
     p.add_argument("--no-config5", dest="config5", action="store_false")
+    p.add_argument("--no-frame", action="store_true", help="skip the frame-layout measurement")
     return p.parse_args()
 
 
@@ -374,6 +375,50 @@ def bench_config5(args, rank, dev, stream, flush, peak):
     return out
 
 
+def bench_frame(args, rank, dev, stream, flush, peak):
+    """Blocks inside frames (no packing step): forward from an int16 residual frame and inverse
+    back into an int16 frame (rounded), on 8 frames of 3840x2160 tiled as in config 3 and
+    stacked into one frame (one launch per direction), median of L2-flushed repeats."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2505_23618_gb300 as adj
+
+    reps = max(3, min(args.steps, 20))
+    n_frames = max(1, args.frames)
+    frame, blocks, tfs = synth.config3_frame(seed=3 + 1000 * rank, frames=n_frames)
+    plan = adj.Plan(tfs)
+    plan.set_frame_blocks(blocks, 3840, frame.shape[0], frame.shape[1])
+    x = torch.from_numpy(frame).to(dev)
+    y = torch.empty(plan.total, dtype=torch.float32, device=dev)
+    r = torch.empty_like(x)
+    coefs = plan.total
+    for _ in range(2):
+        plan.fwd_frame(x, y, stream)
+        plan.inv_frame(y, d_frame_i16=r, stream=stream)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+    for e in ev:
+        flush.fill_(8.0)
+        e[0].record(stream)
+        plan.fwd_frame(x, y, stream)
+        e[1].record(stream)
+        flush.fill_(9.0)
+        e[2].record(stream)
+        plan.inv_frame(y, d_frame_i16=r, stream=stream)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    exact = bool(torch.equal(r[:, :3840], x[:, :3840]))
+    tf = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+    ti = float(np.median([e[2].elapsed_time(e[3]) for e in ev]))
+    plan.close()
+    return {"workload": f"{n_frames} frames 3840x2160 (config-3 tiling) stacked, int16 frame in, int16 frame out",
+            "value": round(coefs / ((tf + ti) * 1e-3) / 1e9, 3), "unit": UNIT, "fwd_ms": round(tf, 4),
+            "inv_ms": round(ti, 4), "fwd_frac": round(coefs * 6 / (tf * 1e-3) / 1e9 / peak, 4),
+            "inv_frac": round(coefs * 6 / (ti * 1e-3) / 1e9 / peak, 4),
+            "int16_roundtrip_exact": exact, "how": f"median of {reps} L2-flushed repeats"}
+
+
 def run_fused(args):
     import numpy as np
     import torch
@@ -468,6 +513,7 @@ def run_fused(args):
     peak, peak_src = measured_peak()
     multiple = bench_multiple(args, rank, dev, stream, flush, peak) if not args.no_multiple else None
     config5 = bench_config5(args, rank, dev, stream, flush, peak) if args.config5 else None
+    frame = bench_frame(args, rank, dev, stream, flush, peak) if not args.no_frame else None
 
     # end to end through the host-buffer C-ABI calls (pinned memory), copies included
     h_x = torch.from_numpy(wl.data).pin_memory()
@@ -519,6 +565,7 @@ def run_fused(args):
             "roofline": roof,
             "multiple": multiple,
             "config5": config5,
+            "frame": frame,
             "kernels": {k: {"ms": round(v["ms"], 4), "GB/s": round(v["gbs"], 1), "frac": round(v["frac"], 4)}
                         for k, v in kern.items()},
             "clocks": clk.summary(),

@@ -146,6 +146,42 @@ int adj_transform_fwd(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, v
 int adj_transform_inv(adj_plan_t* plan, const float* d_coef, float* d_resid_out, void* stream);
 
 /*
+ * Blocks inside a frame.  The adjustments act on W x B and B x H regions of a frame
+ * (Section 2.2); a codec keeps its residual and its reconstruction as frames, so these calls
+ * read each block from its place in a residual frame and write it back to its place,
+ * without a packing step.
+ *
+ * adj_plan_set_frame_blocks gives the plan n_blocks blocks (host memory) of a frame of
+ * frame_w x frame_h samples whose rows are `stride` samples apart (stride >= frame_w, a
+ * multiple of 8; frame buffers 16-B aligned).  A batch of equal frames stored one after
+ * another with the same stride is one frame of (frames x frame_h) rows: one launch then
+ * covers the whole batch.  Block positions (x, y) are multiples of 4, blocks
+ * lie inside the frame and do not overlap; sizes and transform indices follow the rules of
+ * adj_block_t.  The coefficients of the blocks are packed: block i's h x w coefficients
+ * (row-major) start at sample sum_{j<i} w_j h_j, and total_coefs is that sum over all blocks.
+ * (The packed entry points adj_transform_fwd/_inv and the host-buffer ones then work on that
+ * packed layout.)  Errors: INVALID_ARG (also overlaps, blocks outside the frame),
+ * UNSUPPORTED_SIZE, PARAM_MISMATCH, MISALIGNED (positions, stride), CUDA.
+ *
+ * adj_transform_fwd_frame: d_frame (int16 residual frame, device) -> d_coef (FP32, packed as
+ * above, device).  adj_transform_inv_frame: d_coef -> exactly one of d_frame_f32 (FP32) or
+ * d_frame_i16 (rounded to nearest, ties to even, saturated to int16); samples outside every
+ * block are not written.  One persistent launch each, asynchronous on `stream`.
+ * Errors: INVALID_ARG (also: the plan has no frame blocks, both or neither output given),
+ * NO_BLOCKS, MISALIGNED, CUDA.
+ */
+typedef struct {
+  int32_t x, y;    /* top-left sample of the block in the frame */
+  uint16_t w, h;
+  uint16_t tf_h, tf_v;
+} adj_frame_block_t;
+int adj_plan_set_frame_blocks(adj_plan_t* plan, const adj_frame_block_t* blocks, int64_t n_blocks, int32_t frame_w,
+                              int32_t frame_h, int32_t stride);
+int adj_transform_fwd_frame(adj_plan_t* plan, const int16_t* d_frame, float* d_coef, void* stream);
+int adj_transform_inv_frame(adj_plan_t* plan, const float* d_coef, float* d_frame_f32, int16_t* d_frame_i16,
+                            void* stream);
+
+/*
  * Simultaneous DST-7 / DCT-8 adjustments for an encoder's transform search ("Multiple",
  * Section 2.3).  With a post-adjustment after the DCT-2, S T^(C2) = T^(C2) R turns the
  * DCT-8 flip of Eq. 3 into Eq. 5: if C^(S7) = diag(Q, I) adjusts the DCT-2 towards the
@@ -227,7 +263,7 @@ int adj_transform_inv_plain(adj_plan_t* plan, const float* d_coef, float* d_resi
 /*
  * Host-buffer variants: copy the input from host memory to plan-owned device staging
  * buffers, transform, copy the result back and wait for it.  The block list (in storage
- * order) is cut into chunks of about 2 M samples (at most 32); each chunk's input copy,
+ * order) is cut into chunks of about 4 M samples (at most 16); each chunk's input copy,
  * kernel launch and output copy run on three streams, so the copies of one chunk overlap
  * the kernel and copies of the others.  Page-locked host memory gives full copy bandwidth.
  * Samples of h_out outside every block are left unchanged or set to zero.  The staging

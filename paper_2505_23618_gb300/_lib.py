@@ -33,6 +33,7 @@ EXPORTED = (
     "adj_graph_create", "adj_graph_launch", "adj_graph_destroy", "adj_transform_bwd",
     "adj_plan_param_layout", "adj_coding_gain_proxy", "adj_plan_get_tuning", "adj_plan_set_tuning",
     "adj_plan_autotune", "adj_plan_prepare_multiple", "adj_transform_fwd_multiple",
+    "adj_plan_set_frame_blocks", "adj_transform_fwd_frame", "adj_transform_inv_frame",
 )
 DTYPE_INT16, DTYPE_FP32 = 0, 1
 GRAPH_FWD, GRAPH_INV, GRAPH_FWD_PLAIN, GRAPH_INV_PLAIN, GRAPH_ROUNDTRIP, GRAPH_FWD_MULTIPLE = range(6)
@@ -57,6 +58,8 @@ class AdjPlanInfo(C.Structure):
 
 BLOCK_DTYPE = np.dtype([("offset", "<i8"), ("w", "<u2"), ("h", "<u2"),
                         ("tf_h", "<u2"), ("tf_v", "<u2")])
+FRAME_BLOCK_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("w", "<u2"), ("h", "<u2"),
+                              ("tf_h", "<u2"), ("tf_v", "<u2")])  # adj_frame_block_t
 
 
 class AdjError(RuntimeError):
@@ -87,6 +90,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.adj_plan_autotune.argtypes = [vp, vp, vp, vp, C.c_char_p, i32, vp]
     lib.adj_plan_prepare_multiple.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.adj_transform_fwd_multiple.argtypes = [vp, vp, vp, vp, vp]
+    lib.adj_plan_set_frame_blocks.argtypes = [vp, vp, i64, i32, i32, i32]
+    lib.adj_transform_fwd_frame.argtypes = [vp, vp, vp, vp]
+    lib.adj_transform_inv_frame.argtypes = [vp, vp, vp, vp, vp]
     lib.adj_graph_create.argtypes = [vp, i32, vp, vp, vp, C.POINTER(vp)]
     lib.adj_graph_launch.argtypes = [vp, vp]
     lib.adj_graph_destroy.argtypes = [vp]
@@ -197,6 +203,22 @@ class Plan:
 
     def inv(self, d_in, d_out, stream=None):
         check(self._lib.adj_transform_inv(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+    def set_frame_blocks(self, blocks: np.ndarray, frame_w: int, frame_h: int, stride: int):
+        """Blocks inside a frame (FRAME_BLOCK_DTYPE records); coefficients are packed in list order."""
+        b = np.ascontiguousarray(blocks).view(FRAME_BLOCK_DTYPE)
+        check(self._lib.adj_plan_set_frame_blocks(self._h, b.ctypes.data if b.size else None, b.size,
+                                                  int(frame_w), int(frame_h), int(stride)))
+        self.n_blocks = int(b.size)
+        self.total = int(np.sum(b["w"].astype(np.int64) * b["h"])) if b.size else 0
+        return self
+
+    def fwd_frame(self, d_frame, d_coef, stream=None):
+        check(self._lib.adj_transform_fwd_frame(self._h, _ptr(d_frame), _ptr(d_coef), _stream(stream)))
+
+    def inv_frame(self, d_coef, d_frame_f32=None, d_frame_i16=None, stream=None):
+        check(self._lib.adj_transform_inv_frame(self._h, _ptr(d_coef), _ptr(d_frame_f32), _ptr(d_frame_i16),
+                                                _stream(stream)))
 
     def prepare_multiple(self):
         """Validate the block list for the Multiple forward; returns the side offsets in

@@ -54,8 +54,8 @@ struct TfHost {
 // Host-buffer path: the offset-sorted block list is cut into chunks of about
 // kHostChunkCoefs coefficients (at most kMaxHostChunks); chunk c's input copy, kernel and
 // output copy run on three streams, so copies of one chunk overlap the kernel of another.
-constexpr int64_t kHostChunkCoefs = 2 << 20;
-constexpr int kMaxHostChunks = 32;
+constexpr int64_t kHostChunkCoefs = 4 << 20;
+constexpr int kMaxHostChunks = 16;
 struct HostChunk {
   int64_t begin, end;   // samples [begin, end) covered by the chunk's blocks
   int tile0, n_tiles;   // the chunk's tiles in the host tile list
@@ -99,8 +99,13 @@ struct adj_plan {
   // Multiple forward: prepared block list, side offsets in the caller's block order
   bool multi = false;
   std::vector<int64_t> side_off;
-  uint32_t* d_tile_side = nullptr;     // side offset / 4, parallel to d_tile_blk
+  // Blocks inside a frame: frame offsets (y * stride + x) in the caller's block order
+  bool frame = false;
+  int32_t frame_w = 0, frame_h = 0, frame_stride = 0;
+  std::vector<int64_t> frame_off;
+  uint32_t* d_tile_side = nullptr;     // side or frame offset / 4, parallel to d_tile_blk
   int occ_multi = 0, grid_multi = 0;
+  int occ_frame = 0, grid_frame = 0;
   adj_tuning_t tuning{};
   int occ_fwd = 0, occ_inv = 0;        // resident CTAs per SM of the fused kernels
   // host-buffer path (built on first use, dropped with the block layout)
@@ -316,9 +321,34 @@ int run_multi(adj_plan* p, const int16_t* in, float* out, float* side, cudaStrea
   a.n_tiles = p->n_tiles;
   a.n_ranges = p->n_ranges;
   a.side = side;
-  a.tile_side = p->d_tile_side;
+  a.tile_aux = p->d_tile_side;
   cudaError_t e = launch_multi(p->grid_multi, a, stream);
   if (e != cudaSuccess) return cuda_fail(e, "Multiple forward launch");
+  return ADJ_OK;
+}
+
+int run_frame(adj_plan* p, bool inverse, const void* in, void* out, bool i16, cudaStream_t stream) {
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "no block list");
+  if (!p->frame) return fail(ADJ_ERR_INVALID_ARG, "the plan's blocks were not given with adj_plan_set_frame_blocks");
+  int rc;
+  if ((rc = check_ptr(in, "input")) || (rc = check_ptr(out, "output"))) return rc;
+  if (p->n_tiles == 0) return ADJ_OK;
+  FusedArgs a{};
+  a.tiles = p->d_tiles;
+  a.tile_blk = p->d_tile_blk;
+  a.tfs = p->d_tfs;
+  a.params = p->d_params;
+  a.in = in;
+  a.out = static_cast<float*>(out);
+  a.sched = p->d_sched + (inverse ? 1 : 0);
+  a.range_begin = p->d_range_begin;
+  a.n_tiles = p->n_tiles;
+  a.n_ranges = p->n_ranges;
+  a.tile_aux = p->d_tile_side;
+  a.frame_stride = p->frame_stride;
+  cudaError_t e = launch_frame(inverse, i16, p->grid_frame, a, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "frame launch");
   return ADJ_OK;
 }
 
@@ -404,6 +434,7 @@ void apply_grid(adj_plan* p) {
   p->grid_fwd = std::max(1, c > 0 ? std::min(c, p->occ_fwd) : p->occ_fwd) * p->n_sm;
   p->grid_inv = std::max(1, c > 0 ? std::min(c, p->occ_inv) : p->occ_inv) * p->n_sm;
   p->grid_multi = std::max(1, c > 0 ? std::min(c, p->occ_multi) : p->occ_multi) * p->n_sm;
+  p->grid_frame = std::max(1, c > 0 ? std::min(c, p->occ_frame) : p->occ_frame) * p->n_sm;
 }
 
 // Tiles, per-SM ranges and the plain form's per-size lists for the plan's block list,
@@ -456,6 +487,7 @@ void build_tiles(const adj_plan* p, size_t i0, size_t i1, TileSet* ts) {
     if (o.offs.empty()) o.first = b.offset;
     o.offs.push_back((uint32_t)(b.offset / 16));
     if (p->multi) o.sides.push_back((uint32_t)(p->side_off[p->orig[i]] / 4));
+    else if (p->frame) o.sides.push_back((uint32_t)(p->frame_off[p->orig[i]] / 4));
     if ((int)o.offs.size() >= tuned_capacity(p, b.w, b.h)) emit(key, o);
   }
   for (auto& kv : open)
@@ -484,13 +516,13 @@ void build_tiles(const adj_plan* p, size_t i0, size_t i1, TileSet* ts) {
     d.t.blk_begin = (uint32_t)tblk.size();
     tiles.push_back(d.t);
     tblk.insert(tblk.end(), d.offs.begin(), d.offs.end());
-    if (p->multi) {
+    if (p->multi || p->frame) {
       tside.resize(d.t.blk_begin, 0u);
       tside.insert(tside.end(), d.sides.begin(), d.sides.end());
     }
   }
   tblk.resize(tblk.size() + 4, 0u);
-  if (p->multi) tside.resize(tblk.size(), 0u);
+  if (p->multi || p->frame) tside.resize(tblk.size(), 0u);
 
   // Per-SM ranges of this set's tiles (indices relative to its first tile) with about
   // equal numbers of coefficients.
@@ -555,7 +587,7 @@ int build_layout(adj_plan* p) {
     CUDA_TRY(cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(p->d_tile_blk, tblk.data(), tblk.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(p->d_range_begin, rbeg.data(), rbeg.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
-    if (p->multi) {
+    if (p->multi || p->frame) {
       CUDA_TRY(cudaMalloc(&p->d_tile_side, tside.size() * sizeof(uint32_t)));
       CUDA_TRY(cudaMemcpy(p->d_tile_side, tside.data(), tside.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     }
@@ -802,6 +834,14 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
     else p->occ_multi = std::max(1, occ);
   }
+  for (int v = 0; v < 3 && !rc; ++v) {  // frame forward, inverse FP32, inverse int16
+    const void* fn = frame_kernel_ptr(v > 0, v == 2);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
+    if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
+    else p->occ_frame = v == 0 ? std::max(1, occ) : std::min(p->occ_frame, std::max(1, occ));
+  }
   if (!rc) {
     for (int i = 0; i < 25; ++i) p->tuning.cap_div[i] = 1;
     p->tuning.ctas_per_sm = 0;
@@ -866,6 +906,8 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
   p->orig = order;
   p->multi = false;
   p->side_off.clear();
+  p->frame = false;
+  p->frame_off.clear();
   p->n_blocks = n_blocks;
   p->total = total_coefs;
   const int rc = build_layout(p);
@@ -884,10 +926,80 @@ int adj_transform_inv(adj_plan_t* p, const float* d_coef, float* d_resid_out, vo
   return run(p, true, d_coef, d_resid_out, static_cast<cudaStream_t>(stream));
 }
 
+int adj_plan_set_frame_blocks(adj_plan_t* p, const adj_frame_block_t* blocks, int64_t n_blocks, int32_t frame_w,
+                              int32_t frame_h, int32_t stride) {
+  g_err.clear();
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (n_blocks < 0 || (n_blocks > 0 && !blocks)) return fail(ADJ_ERR_INVALID_ARG, "bad block list");
+  if (frame_w <= 0 || frame_h <= 0 || frame_w % 4 || frame_h % 4)
+    return fail(ADJ_ERR_INVALID_ARG, "frame %dx%d: sides must be positive multiples of 4", frame_w, frame_h);
+  if (stride < frame_w || stride % 8) return fail(ADJ_ERR_MISALIGNED, "frame stride %d: must be >= the width and a multiple of 8", stride);
+  if ((int64_t)stride * frame_h > (int64_t(1) << 34)) return fail(ADJ_ERR_INVALID_ARG, "frame too large");
+  const int n_tfs = (int)p->tfs.size();
+  const int gw = frame_w / 4, gh = frame_h / 4;
+  std::vector<uint8_t> cover((size_t)gw * gh, 0);  // 4 x 4 cells already taken
+  std::vector<adj_block_t> packed(n_blocks);
+  std::vector<int64_t> foff(n_blocks);
+  int64_t total = 0;
+  for (int64_t i = 0; i < n_blocks; ++i) {
+    const adj_frame_block_t& b = blocks[i];
+    if (!is_size(b.w) || !is_size(b.h)) return fail(ADJ_ERR_UNSUPPORTED_SIZE, "block %lld: %dx%d", (long long)i, b.w, b.h);
+    if (b.tf_h >= n_tfs || b.tf_v >= n_tfs) return fail(ADJ_ERR_INVALID_ARG, "block %lld: transform index out of range", (long long)i);
+    if (p->tfs[b.tf_h].n != b.w || p->tfs[b.tf_v].n != b.h)
+      return fail(ADJ_ERR_PARAM_MISMATCH, "block %lld: %dx%d with transforms of length %d (h) and %d (v)", (long long)i, b.w,
+                  b.h, p->tfs[b.tf_h].n, p->tfs[b.tf_v].n);
+    if (b.x < 0 || b.y < 0 || b.x % 4 || b.y % 4)
+      return fail(ADJ_ERR_MISALIGNED, "block %lld at (%d, %d): positions must be non-negative multiples of 4", (long long)i, b.x, b.y);
+    if (b.x + b.w > frame_w || b.y + b.h > frame_h)
+      return fail(ADJ_ERR_INVALID_ARG, "block %lld at (%d, %d) leaves the %dx%d frame", (long long)i, b.x, b.y, frame_w, frame_h);
+    for (int cy = b.y / 4; cy < (b.y + b.h) / 4; ++cy)
+      for (int cx = b.x / 4; cx < (b.x + b.w) / 4; ++cx) {
+        uint8_t& c = cover[(size_t)cy * gw + cx];
+        if (c) return fail(ADJ_ERR_INVALID_ARG, "block %lld overlaps an earlier block", (long long)i);
+        c = 1;
+      }
+    packed[i] = adj_block_t{total, b.w, b.h, b.tf_h, b.tf_v};
+    foff[i] = (int64_t)b.y * stride + b.x;
+    total += (int64_t)b.w * b.h;
+  }
+  (void)gh;
+  // the packed list is in storage order already (offsets increase with the list index)
+  p->blocks = packed;
+  p->orig.resize(n_blocks);
+  for (int64_t i = 0; i < n_blocks; ++i) p->orig[i] = i;
+  p->n_blocks = n_blocks;
+  p->total = total;
+  p->multi = false;
+  p->side_off.clear();
+  p->frame = true;
+  p->frame_w = frame_w;
+  p->frame_h = frame_h;
+  p->frame_stride = stride;
+  p->frame_off = foff;
+  const int rc = build_layout(p);
+  if (rc) return rc;
+  p->has_blocks = true;
+  return ADJ_OK;
+}
+
+int adj_transform_fwd_frame(adj_plan_t* p, const int16_t* d_frame, float* d_coef, void* stream) {
+  g_err.clear();
+  return run_frame(p, false, d_frame, d_coef, false, static_cast<cudaStream_t>(stream));
+}
+
+int adj_transform_inv_frame(adj_plan_t* p, const float* d_coef, float* d_frame_f32, int16_t* d_frame_i16,
+                            void* stream) {
+  g_err.clear();
+  if (!!d_frame_f32 == !!d_frame_i16) return fail(ADJ_ERR_INVALID_ARG, "give exactly one of the FP32 and int16 outputs");
+  if (d_frame_f32) return run_frame(p, true, d_coef, d_frame_f32, false, static_cast<cudaStream_t>(stream));
+  return run_frame(p, true, d_coef, d_frame_i16, true, static_cast<cudaStream_t>(stream));
+}
+
 int adj_plan_prepare_multiple(adj_plan_t* p, int64_t* side_offsets, int64_t* side_total) {
   g_err.clear();
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
   if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  if (p->frame) return fail(ADJ_ERR_INVALID_ARG, "the Multiple forward takes a packed block list, not frame blocks");
   auto k_of = [&](int t) { return p->tfs[t].kind == ADJ_ADJ_POST_BLOCK ? p->tfs[t].k : 0; };
   std::vector<int64_t> size(p->blocks.size());
   for (size_t s = 0; s < p->blocks.size(); ++s) {

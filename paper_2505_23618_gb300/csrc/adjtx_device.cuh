@@ -129,9 +129,45 @@ __device__ __forceinline__ void q_quad(const float* P, const TfDev& tf, int i, i
   q[2] = make_float2(b.x, b.y); q[3] = make_float2(b.z, b.w);
 }
 
+// One line per thread (T = float): the K-long dot products run in packed FP32x2 along the
+// inputs, {acc_even, acc_odd} += {Q[i][j], Q[i][j+1]} * {v_j, v_{j+1}}, which halves the FMA
+// instructions; the two halves are added at the end of each row.
+template <int N, int KT, class Dst>
+__device__ __forceinline__ void post_fwd_k1(const float (&v)[N], const TfDev& tf, const float* __restrict__ P,
+                                            const Dst& dst) {
+  constexpr int R = PostRows<KT, float>::R;
+#pragma unroll
+  for (int i = KT; i < N; ++i) dst.put(i, v[i]);
+#pragma unroll 1
+  for (int i = 0; i < KT; i += R) {
+    float2 acc[R][2];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int g = 0; g < KT / 4; ++g) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float q[4];
+        q_quad(P, tf, i + r, g, q);
+        acc[r][0] = __ffma2_rn(make_float2(q[0], q[1]), make_float2(v[4 * g], v[4 * g + 1]), acc[r][0]);
+        acc[r][1] = __ffma2_rn(make_float2(q[2], q[3]), make_float2(v[4 * g + 2], v[4 * g + 3]), acc[r][1]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float2 t = __fadd2_rn(acc[r][0], acc[r][1]);
+      dst.put_rt(i + r, t.x + t.y);
+    }
+  }
+}
+
 template <int N, int KT, class T, class Dst>
 __device__ __forceinline__ void post_fwd_k(const T (&v)[N], const TfDev& tf, const float* __restrict__ P,
                                            const Dst& dst) {
+  if constexpr (sizeof(T) == 4) {
+    post_fwd_k1<N, KT>(v, tf, P, dst);
+    return;
+  }
   constexpr int R = PostRows<KT, T>::R;
 #pragma unroll
   for (int i = KT; i < N; ++i) dst.put(i, v[i]);
@@ -158,8 +194,47 @@ __device__ __forceinline__ void post_fwd_k(const T (&v)[N], const TfDev& tf, con
   }
 }
 
+// One line per thread: u_j = sum_i Q[i][j] y_i accumulated as pairs {u_j, u_{j+1}} in packed
+// FP32x2, with y_i broadcast to both halves.
+template <int N, int KT, class Src>
+__device__ __forceinline__ void post_inv_k1(float (&v)[N], const TfDev& tf, const float* __restrict__ P,
+                                            const Src& src) {
+  constexpr int R = PostRows<KT, float>::R;
+  float2 u[KT / 2];
+#pragma unroll
+  for (int m = 0; m < KT / 2; ++m) u[m] = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int i = 0; i < KT; i += R) {
+    float2 y[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float t = src.get_rt(i + r);
+      y[r] = make_float2(t, t);
+    }
+#pragma unroll
+    for (int g = 0; g < KT / 4; ++g) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float q[4];
+        q_quad(P, tf, i + r, g, q);
+        u[2 * g] = __ffma2_rn(make_float2(q[0], q[1]), y[r], u[2 * g]);
+        u[2 * g + 1] = __ffma2_rn(make_float2(q[2], q[3]), y[r], u[2 * g + 1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < KT / 2; ++m) {
+    v[2 * m] = u[m].x;
+    v[2 * m + 1] = u[m].y;
+  }
+}
+
 template <int N, int KT, class T, class Src>
 __device__ __forceinline__ void post_inv_k(T (&v)[N], const TfDev& tf, const float* __restrict__ P, const Src& src) {
+  if constexpr (sizeof(T) == 4) {
+    post_inv_k1<N, KT>(v, tf, P, src);
+    return;
+  }
   constexpr int R = PostRows<KT, T>::R;
 #pragma unroll
   for (int j = 0; j < KT; ++j) v[j] = vzero(v[0]);
@@ -308,6 +383,60 @@ struct DstGCol2 {
   __device__ __forceinline__ void store(const float2 (&v)[N]) const {
 #pragma unroll
     for (int i = 0; i < N; ++i) *reinterpret_cast<float2*>(p + i * S) = v[i];
+  }
+};
+
+// Output columns of a block inside a frame (run-time row stride): FP32, or rounded to the
+// nearest integer (ties to even) and saturated to int16.  The pair forms write columns c and
+// c + 1 (c even) with one 8-byte (FP32) or 4-byte (int16) store.
+__device__ __forceinline__ short sat16(float x) {
+  const int v = __float2int_rn(x);
+  return (short)(v < -32768 ? -32768 : (v > 32767 ? 32767 : v));
+}
+struct DstFrame {
+  float* p;
+  int s;
+  __device__ __forceinline__ void put(int i, float x) const { p[(size_t)i * s] = x; }
+  __device__ __forceinline__ void put_rt(int i, float x) const { p[(size_t)i * s] = x; }
+  template <int N>
+  __device__ __forceinline__ void store(const float (&v)[N]) const {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[(size_t)i * s] = v[i];
+  }
+};
+struct DstFrame2 {
+  float* p;
+  int s;
+  __device__ __forceinline__ void put(int i, float2 x) const { *reinterpret_cast<float2*>(p + (size_t)i * s) = x; }
+  __device__ __forceinline__ void put_rt(int i, float2 x) const { *reinterpret_cast<float2*>(p + (size_t)i * s) = x; }
+  template <int N>
+  __device__ __forceinline__ void store(const float2 (&v)[N]) const {
+#pragma unroll
+    for (int i = 0; i < N; ++i) *reinterpret_cast<float2*>(p + (size_t)i * s) = v[i];
+  }
+};
+struct DstFrameI16 {
+  short* p;
+  int s;
+  __device__ __forceinline__ void put(int i, float x) const { p[(size_t)i * s] = sat16(x); }
+  __device__ __forceinline__ void put_rt(int i, float x) const { p[(size_t)i * s] = sat16(x); }
+  template <int N>
+  __device__ __forceinline__ void store(const float (&v)[N]) const {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[(size_t)i * s] = sat16(v[i]);
+  }
+};
+struct DstFrameI16x2 {
+  short* p;
+  int s;
+  __device__ __forceinline__ void put(int i, float2 x) const {
+    *reinterpret_cast<short2*>(p + (size_t)i * s) = make_short2(sat16(x.x), sat16(x.y));
+  }
+  __device__ __forceinline__ void put_rt(int i, float2 x) const { put(i, x); }
+  template <int N>
+  __device__ __forceinline__ void store(const float2 (&v)[N]) const {
+#pragma unroll
+    for (int i = 0; i < N; ++i) put(i, v[i]);
   }
 };
 

@@ -64,6 +64,53 @@ __device__ __forceinline__ void stage_tile_w(const TileDev& td, const uint32_t* 
   }
 }
 
+// Forward from a frame: block b's row r starts at sample (aux_b * 4 + r * stride) of the int16
+// frame (stride a multiple of 8).  Each 8-sample chunk q of a row goes to its chunk slot
+// q ^ f(r) as one 16-byte copy when the block starts on an 8-sample boundary, else as two
+// 8-byte copies (blocks sit on a 4-sample grid); 4-wide rows are one 8-byte copy.
+template <int W, int THREADS>
+__device__ __forceinline__ void stage_frame_w(const TileDev& td, const uint32_t* sAux, const int16_t* frame,
+                                              int64_t stride, float* buf) {
+  constexpr int SH = sw_shift(W), MK = sw_mask(W);
+  const int h = td.h, nb = td.nblk, lgh = lg2(h);
+  if constexpr (W == 4) {
+    const int total = nb << lgh;
+    for (int g = threadIdx.x; g < total; g += THREADS) {
+      const int b = g >> lgh, r = g & (h - 1);
+      cp_async8(buf + b * 4 * h + r * 4, frame + (size_t)sAux[b] * 4 + (size_t)r * stride);
+    }
+  } else {
+    constexpr int LG_CPR = ilog2(W / 8);
+    const int lg_cpb = LG_CPR + lgh, total = nb << lg_cpb;
+    for (int g = threadIdx.x; g < total; g += THREADS) {
+      const int b = g >> lg_cpb, gg = g & ((1 << lg_cpb) - 1);
+      const int r = gg >> LG_CPR, q = gg & ((1 << LG_CPR) - 1);
+      const uint32_t a = sAux[b];
+      const int16_t* src = frame + (size_t)a * 4 + (size_t)r * stride + q * 8;
+      float* dst = buf + (b << (lgh + ilog2(W))) + r * W + ((q ^ ((r >> SH) & MK)) << 2);
+      if ((a & 1u) == 0) {
+        cp_async16(dst, src);
+      } else {
+        cp_async8(dst, src);
+        cp_async8(dst + 2, src + 4);
+      }
+    }
+  }
+}
+
+template <int THREADS>
+__device__ __forceinline__ void stage_frame(const TileDev& td, const uint32_t* sAux, const void* in, int64_t stride,
+                                            float* buf) {
+  const int16_t* frame = static_cast<const int16_t*>(in);
+  switch (td.w) {
+    case 4: stage_frame_w<4, THREADS>(td, sAux, frame, stride, buf); break;
+    case 8: stage_frame_w<8, THREADS>(td, sAux, frame, stride, buf); break;
+    case 16: stage_frame_w<16, THREADS>(td, sAux, frame, stride, buf); break;
+    case 32: stage_frame_w<32, THREADS>(td, sAux, frame, stride, buf); break;
+    default: stage_frame_w<64, THREADS>(td, sAux, frame, stride, buf); break;
+  }
+}
+
 template <bool INV, int THREADS>
 __device__ __forceinline__ void stage_tile(const TileDev& td, const uint32_t* sOff, const void* in, float* buf) {
   switch (td.w) {
@@ -98,9 +145,12 @@ __device__ __forceinline__ void row_pass(const TfDev& tf, const float* __restric
   }
 }
 
-template <int H, int W, bool INV, int THREADS>
+// Output of the column pass: packed blocks (OUT 0, at sOff[b] * 16), or blocks inside a
+// frame (at sAux[b] * 4, row stride `stride`) as FP32 (OUT 1) or rounded int16 (OUT 2).
+template <int H, int W, bool INV, int THREADS, int OUT>
 __device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restrict__ P, const float* buf,
-                                         const uint32_t* sOff, float* __restrict__ out, int nb) {
+                                         const uint32_t* sOff, const uint32_t* sAux, float* __restrict__ out, int nb,
+                                         int stride) {
   constexpr int lgw = ilog2(W);
   const int nlines = nb * W;
   if constexpr (H <= 32) {
@@ -109,28 +159,41 @@ __device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restric
     for (int l = threadIdx.x; l < pairs; l += THREADS) {
       const int b = (2 * l) >> lgw, c = (2 * l) & (W - 1);
       const ColSw2<W> src(buf + b * (W * H), c);
-      const DstGCol2<W> dst{out + (size_t)sOff[b] * 16 + c};
-      line_transform<H, INV, false, float2>(tf, P, src, dst);
+      if constexpr (OUT == 0) {
+        line_transform<H, INV, false, float2>(tf, P, src, DstGCol2<W>{out + (size_t)sOff[b] * 16 + c});
+      } else if constexpr (OUT == 1) {
+        line_transform<H, INV, false, float2>(tf, P, src, DstFrame2{out + (size_t)sAux[b] * 4 + c, stride});
+      } else {
+        short* o16 = reinterpret_cast<short*>(out);
+        line_transform<H, INV, false, float2>(tf, P, src, DstFrameI16x2{o16 + (size_t)sAux[b] * 4 + c, stride});
+      }
     }
   } else {
     for (int l = threadIdx.x; l < nlines; l += THREADS) {
       const int b = l >> lgw, c = l & (W - 1);
       ColSw<W> src(buf + b * (W * H), c);
-      DstGCol<W> dst{out + (size_t)sOff[b] * 16 + c};
-      line_transform<H, INV, false>(tf, P, src, dst);
+      if constexpr (OUT == 0) {
+        line_transform<H, INV, false>(tf, P, src, DstGCol<W>{out + (size_t)sOff[b] * 16 + c});
+      } else if constexpr (OUT == 1) {
+        line_transform<H, INV, false>(tf, P, src, DstFrame{out + (size_t)sAux[b] * 4 + c, stride});
+      } else {
+        short* o16 = reinterpret_cast<short*>(out);
+        line_transform<H, INV, false>(tf, P, src, DstFrameI16{o16 + (size_t)sAux[b] * 4 + c, stride});
+      }
     }
   }
 }
 
-template <int H, bool INV, int THREADS>
+template <int H, bool INV, int THREADS, int OUT>
 __device__ __forceinline__ void col_dispatch(const TfDev& tf, const float* __restrict__ P, const float* buf,
-                                             const uint32_t* sOff, float* __restrict__ out, int nb, int w) {
+                                             const uint32_t* sOff, const uint32_t* sAux, float* __restrict__ out,
+                                             int nb, int w, int stride) {
   switch (w) {
-    case 4: col_pass<H, 4, INV, THREADS>(tf, P, buf, sOff, out, nb); break;
-    case 8: col_pass<H, 8, INV, THREADS>(tf, P, buf, sOff, out, nb); break;
-    case 16: col_pass<H, 16, INV, THREADS>(tf, P, buf, sOff, out, nb); break;
-    case 32: col_pass<H, 32, INV, THREADS>(tf, P, buf, sOff, out, nb); break;
-    default: col_pass<H, 64, INV, THREADS>(tf, P, buf, sOff, out, nb); break;
+    case 4: col_pass<H, 4, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
+    case 8: col_pass<H, 8, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
+    case 16: col_pass<H, 16, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
+    case 32: col_pass<H, 32, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
+    default: col_pass<H, 64, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
   }
 }
 
@@ -165,25 +228,25 @@ __device__ __forceinline__ void split_post_k(const float (&v)[N], const TfDev& t
   constexpr int R = PostRows<KT, float>::R;
 #pragma unroll 1
   for (int i = 0; i < k; i += R) {
-    float acc[R][4];  // by position in a Q quad: 0, 2 even columns, 1, 3 odd columns
+    // packed FP32x2 along the inputs: the .x halves sum the even columns, .y the odd ones
+    float2 acc[R][2];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int x = 0; x < 4; ++x) acc[r][x] = 0.f;
+    for (int r = 0; r < R; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int g = 0; g < KT / 4; ++g) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float q[4];
         q_quad(P, tf, i + r, g, q);
-#pragma unroll
-        for (int x = 0; x < 4; ++x) acc[r][x] = fmaf(q[x], v[4 * g + x], acc[r][x]);
+        acc[r][0] = __ffma2_rn(make_float2(q[0], q[1]), make_float2(v[4 * g], v[4 * g + 1]), acc[r][0]);
+        acc[r][1] = __ffma2_rn(make_float2(q[2], q[3]), make_float2(v[4 * g + 2], v[4 * g + 3]), acc[r][1]);
       }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int ii = i + r;
-      const float e = acc[r][0] + acc[r][2], o = acc[r][1] + acc[r][3];
+      const float2 t = __fadd2_rn(acc[r][0], acc[r][1]);
+      const float e = t.x, o = t.y;
       if (ii < k) emit(ii, e + o, (ii & 1) ? o - e : e - o);
     }
   }
@@ -323,19 +386,25 @@ __device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes
     cp_async16(static_cast<unsigned char*>(dst) + i, static_cast<const unsigned char*>(src) + i);
 }
 
-template <bool INV, int THREADS, bool MULTI = false>
+template <bool INV, int THREADS, int MODE = kModePacked>
 __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_kernel(FusedArgs a) {
+  constexpr bool MULTI = MODE == kModeMulti;
+  constexpr bool FRAME_IN = !INV && MODE == kModeFrame;   // forward reading blocks from a frame
+  constexpr int OUT = !INV || MODE < kModeFrame ? 0 : (MODE == kModeFrame ? 1 : 2);
+  constexpr bool AUX = MODE != kModePacked;
   static_assert(!(INV && MULTI), "the Multiple form is forward only");
+  static_assert(INV || MODE != kModeFrameI16, "int16 output is for the inverse");
   extern __shared__ __align__(16) unsigned char smem[];
   // Records of this CTA's tiles, by the tile's sequence number k in the CTA:
   //   sDesc[k % 4]   descriptor (k .. k+2 are valid at the top of iteration k; k+3 arrives)
   //   sOff[k % 3]    block offsets / 16 (k, k+1 valid; k+2 arrives); a tile's list starts at
   //                  entry blk_begin & 3 (it is copied from the 16-byte aligned address below)
   //   sTf[k % 2]     (horizontal, vertical) transform records (k valid; k+1 arrives)
-  //   sSide[k % 2]   Multiple form: side offsets / 4, indexed like sOff (k valid; k+1 arrives)
+  //   sAux[k % 2]    Multiple / frame modes: side or frame offsets / 4, indexed like sOff
+  //                  (k valid; k+1 arrives; the frame forward also needs k+1 for staging)
   // and tile k's data in buffer k % 2 while tile k+1 is being copied into the other one.
   __shared__ __align__(16) uint32_t sOff[3][kMaxTileBlocks + 4];
-  __shared__ __align__(16) uint32_t sSide[MULTI ? 2 : 1][MULTI ? kMaxTileBlocks + 4 : 4];
+  __shared__ __align__(16) uint32_t sAux[AUX ? 3 : 1][AUX ? kMaxTileBlocks + 4 : 4];
   __shared__ __align__(16) TfDev sTf[2][2];
   __shared__ __align__(16) TileDev sDesc[4];
   __shared__ int sIdx[3];
@@ -366,15 +435,20 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
       sTf[0][1] = a.tfs[d0.tf_v];
     }
     for (int b = tid; b < d0.nblk; b += THREADS) sOff[0][(d0.blk_begin & 3) + b] = a.tile_blk[d0.blk_begin + b];
-    if constexpr (MULTI) {
-      for (int b = tid; b < d0.nblk; b += THREADS) sSide[0][(d0.blk_begin & 3) + b] = a.tile_side[d0.blk_begin + b];
+    if constexpr (AUX) {
+      for (int b = tid; b < d0.nblk; b += THREADS) sAux[0][(d0.blk_begin & 3) + b] = a.tile_aux[d0.blk_begin + b];
     }
     __syncthreads();
-    stage_tile<INV, THREADS>(d0, sOff[0] + (d0.blk_begin & 3), a.in, reinterpret_cast<float*>(smem));
+    if constexpr (FRAME_IN) {
+      stage_frame<THREADS>(d0, sAux[0] + (d0.blk_begin & 3), a.in, a.frame_stride, reinterpret_cast<float*>(smem));
+    } else {
+      stage_tile<INV, THREADS>(d0, sOff[0] + (d0.blk_begin & 3), a.in, reinterpret_cast<float*>(smem));
+    }
     if (tn >= 0) {
       const TileDev d1 = a.tiles[tn];
       if (tid == 0) sDesc[1] = d1;
       copy_async<THREADS>(sOff[1], a.tile_blk + (d1.blk_begin & ~3u), list_bytes(d1));
+      if constexpr (AUX) copy_async<THREADS>(sAux[1], a.tile_aux + (d1.blk_begin & ~3u), list_bytes(d1));
     }
     if (tn2 >= 0 && tid == 0) cp_async16(&sDesc[2], a.tiles + tn2);
     cp_async_commit();
@@ -395,15 +469,19 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
     // (2)
     if (tn >= 0) {
       const TileDev dn = sDesc[(k + 1) & 3];
-      stage_tile<INV, THREADS>(dn, sOff[(k + 1) % 3] + (dn.blk_begin & 3), a.in,
-                               reinterpret_cast<float*>(smem + (cur ^ 1) * kBufBytes));
+      float* nbuf = reinterpret_cast<float*>(smem + (cur ^ 1) * kBufBytes);
+      if constexpr (FRAME_IN) {
+        stage_frame<THREADS>(dn, sAux[(k + 1) % 3] + (dn.blk_begin & 3), a.in, a.frame_stride, nbuf);
+      } else {
+        stage_tile<INV, THREADS>(dn, sOff[(k + 1) % 3] + (dn.blk_begin & 3), a.in, nbuf);
+      }
       copy_async<THREADS>(&sTf[cur ^ 1][0], a.tfs + dn.tf_h, sizeof(TfDev));
       copy_async<THREADS>(&sTf[cur ^ 1][1], a.tfs + dn.tf_v, sizeof(TfDev));
-      if constexpr (MULTI) copy_async<THREADS>(sSide[cur ^ 1], a.tile_side + (dn.blk_begin & ~3u), list_bytes(dn));
     }
     if (tn2 >= 0) {
       const TileDev dn2 = sDesc[(k + 2) & 3];
       copy_async<THREADS>(sOff[(k + 2) % 3], a.tile_blk + (dn2.blk_begin & ~3u), list_bytes(dn2));
+      if constexpr (AUX) copy_async<THREADS>(sAux[(k + 2) % 3], a.tile_aux + (dn2.blk_begin & ~3u), list_bytes(dn2));
     }
     // sIdx[0] is free: every thread read it after the previous iteration's barrier (4)
     if (tid < 32) {
@@ -435,7 +513,7 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
     // (5) column pass (vertical transform, length h), stores to global memory
     const uint32_t* offs = sOff[k % 3] + (td.blk_begin & 3);
     if constexpr (MULTI) {
-      const uint32_t* sides = sSide[cur] + (td.blk_begin & 3);
+      const uint32_t* sides = sAux[k % 3] + (td.blk_begin & 3);
       const TfDev th = sTf[cur][0], tv = sTf[cur][1];
       switch (h) {
         case 4: multi_after_rows<4, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
@@ -446,12 +524,14 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
       }
     } else {
       const TfDev tf = sTf[cur][1];
+      const uint32_t* aux = sAux[AUX ? k % 3 : 0] + (td.blk_begin & 3);
+      const int st = (int)a.frame_stride;
       switch (h) {
-        case 4: col_dispatch<4, INV, THREADS>(tf, a.params, buf, offs, a.out, nb, w); break;
-        case 8: col_dispatch<8, INV, THREADS>(tf, a.params, buf, offs, a.out, nb, w); break;
-        case 16: col_dispatch<16, INV, THREADS>(tf, a.params, buf, offs, a.out, nb, w); break;
-        case 32: col_dispatch<32, INV, THREADS>(tf, a.params, buf, offs, a.out, nb, w); break;
-        default: col_dispatch<64, INV, THREADS>(tf, a.params, buf, offs, a.out, nb, w); break;
+        case 4: col_dispatch<4, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+        case 8: col_dispatch<8, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+        case 16: col_dispatch<16, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+        case 32: col_dispatch<32, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+        default: col_dispatch<64, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
       }
     }
     t = tn;

@@ -19,10 +19,15 @@ struct FusedArgs {
   const unsigned* range_begin;  // n_ranges + 1 tile indices
   int n_tiles;
   int n_ranges;
-  // Multiple forward only: side buffer and the side offsets / 4, parallel to tile_blk
-  float* side;
-  const uint32_t* tile_side;
+  // Per-block auxiliary offsets / 4, parallel to tile_blk: the side offsets of the Multiple
+  // forward, or the frame offsets (y * frame_stride + x) of blocks inside a frame
+  const uint32_t* tile_aux;
+  float* side;                // Multiple forward: side buffer
+  int64_t frame_stride;       // frame modes: samples per frame row
 };
+
+// Kernel modes (template argument of the fused kernel).
+enum { kModePacked = 0, kModeMulti = 1, kModeFrame = 2, kModeFrameI16 = 3 };
 
 // Plain (unfused) form: the blocks of one size class, each with its own transforms.
 struct PlainBlock {
@@ -59,6 +64,9 @@ cudaError_t launch_bwd(bool i16, int grid, const BwdArgs& args, double* M, const
 const void* fused_kernel_ptr(bool inverse, int threads);
 const void* multi_kernel_ptr();
 cudaError_t launch_multi(int grid, const FusedArgs& args, cudaStream_t stream);
+// frame modes: forward reads int16 blocks from a frame; inverse writes FP32 or rounded int16
+const void* frame_kernel_ptr(bool inverse, bool i16);
+cudaError_t launch_frame(bool inverse, bool i16, int grid, const FusedArgs& args, cudaStream_t stream);
 const void* fused_fwd_ptr();
 const void* fused_inv_ptr();
 void set_last_error(const char* msg);

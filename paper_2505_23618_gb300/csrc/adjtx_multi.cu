@@ -3,7 +3,7 @@
 
 namespace adjtx {
 
-const void* multi_kernel_ptr() { return reinterpret_cast<const void*>(&fused_kernel<false, 64, true>); }
+const void* multi_kernel_ptr() { return reinterpret_cast<const void*>(&fused_kernel<false, 64, kModeMulti>); }
 
 cudaError_t launch_multi(int grid, const FusedArgs& args, cudaStream_t stream) {
   FusedArgs a = args;

@@ -249,6 +249,79 @@ def config3(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 216
                     "per-block core x adjustment in each direction, 10-bit AR(1)")
 
 
+FRAME_BLOCK_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("w", "<u2"), ("h", "<u2"),
+                              ("tf_h", "<u2"), ("tf_v", "<u2")])
+
+
+def ctu_frame_blocks(rng, width: int, height: int):
+    """Positions and sizes of the blocks of one frame tiled like config 3 (``_ctu_sizes``):
+    (x, y, w, h) arrays, CTUs in raster order, blocks in raster order inside a CTU region."""
+    cols = width // 64
+    full_rows, rem = divmod(height, 64)
+    regions = []
+    r = rem
+    for s in (32, 16, 8, 4):
+        if r >= s:
+            regions.append(s)
+            r -= s
+    assert r == 0, "frame height must be a multiple of 4"
+    sizes = np.array(SIZES)
+    xs, ys, ws, hs = [], [], [], []
+    for cy in range(full_rows + (1 if rem else 0)):
+        reg = [64] if cy < full_rows else regions
+        for cx in range(cols):
+            W = int(rng.choice(sizes, p=_CTU_P))
+            H = int(rng.choice(sizes, p=_CTU_P))
+            y0 = cy * 64
+            for rh in reg:
+                hh = min(H, rh)
+                for by in range(rh // hh):
+                    for bx in range(64 // W):
+                        xs.append(cx * 64 + bx * W)
+                        ys.append(y0 + by * hh)
+                        ws.append(W)
+                        hs.append(hh)
+                y0 += rh
+    return np.array(xs), np.array(ys), np.array(ws), np.array(hs)
+
+
+def config3_frame(seed: int = 3, width: int = 3840, height: int = 2160, stride: int | None = None,
+                  frames: int = 1):
+    """Config-3 frames in frame layout: (frame int16 [frames * height, stride], frame blocks, tfs).
+
+    The blocks tile each frame as in config 3 (per-CTU sizes, per-block core x adjustment in
+    each direction, 10-bit AR(1) residual per block); ``stride`` (default: width rounded up to
+    a multiple of 64) leaves unused samples at the end of every row.  Several frames are
+    stacked one below the other, which makes them one taller frame with the same stride."""
+    rng = np.random.default_rng(seed)
+    tfs, ids = mixed_tf_table(rng)
+    parts = [ctu_frame_blocks(rng, width, height) for _ in range(frames)]
+    x = np.concatenate([p[0] for p in parts])
+    y = np.concatenate([p[1] + f * height for f, p in enumerate(parts)])
+    w = np.concatenate([p[2] for p in parts])
+    h = np.concatenate([p[3] for p in parts])
+    nb = w.size
+    ch, kh = rng.integers(0, 4, nb), rng.integers(0, 3, nb)
+    cv, kv = rng.integers(0, 4, nb), rng.integers(0, 3, nb)
+    lut_h = np.full((65, 4, 3), -1)
+    lut_v = np.full((65, 4, 3), -1)
+    for (d, n, c, k), i in ids.items():
+        (lut_h if d == "h" else lut_v)[n, c, k] = i
+    packed, data = _pack((w, h, lut_h[w, ch, kh], lut_v[h, cv, kv]), rng, _stats_c2, 1023)
+    stride = stride or (width + 63) // 64 * 64
+    frame = np.zeros((frames * height, stride), dtype=np.int16)
+    blocks = np.zeros(nb, dtype=FRAME_BLOCK_DTYPE)
+    blocks["x"], blocks["y"], blocks["w"], blocks["h"] = x, y, w, h
+    blocks["tf_h"], blocks["tf_v"] = packed["tf_h"], packed["tf_v"]
+    for (ww, hh) in sorted(set(zip(w.tolist(), h.tolist()))):
+        sel = np.nonzero((w == ww) & (h == hh))[0]
+        vals = data[packed["offset"][sel, None] + np.arange(ww * hh)[None, :]].reshape(-1, hh, ww)
+        rows = y[sel, None, None] + np.arange(hh)[None, :, None]
+        cols = x[sel, None, None] + np.arange(ww)[None, None, :]
+        frame[rows, cols] = vals
+    return frame, blocks, tfs
+
+
 def config3_multiple(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 2160,
                      k_max: int = 8) -> Workload:
     """The config-3 frame tiling for the encoder's DST-7 / DCT-8 search (Section 2.3):
