@@ -263,9 +263,9 @@ int adj_transform_inv_plain(adj_plan_t* plan, const float* d_coef, float* d_resi
 /*
  * Host-buffer variants: copy the input from host memory to plan-owned device staging
  * buffers, transform, copy the result back and wait for it.  The block list (in storage
- * order) is cut into chunks of about 4 M samples (at most 16); each chunk's input copy,
- * kernel launch and output copy run on three streams, so the copies of one chunk overlap
- * the kernel and copies of the others.  Page-locked host memory gives full copy bandwidth.
+ * order) is cut into chunks of up to about 4 M samples, shorter at both ends; each chunk's
+ * input copy, kernel launch and output copy run on three streams, so the copies of one chunk
+ * overlap the kernel and copies of the others.  Page-locked host memory gives full copy bandwidth.
  * Samples of h_out outside every block are left unchanged or set to zero.  The staging
  * buffers, chunk tile lists, two streams and their events are allocated on the first call
  * (and the chunk lists again after the block list or the tuning changes).

@@ -51,9 +51,10 @@ struct TfHost {
   std::vector<double> q;  // k x k
 };
 
-// Host-buffer path: the offset-sorted block list is cut into chunks of about
-// kHostChunkCoefs coefficients (at most kMaxHostChunks); chunk c's input copy, kernel and
-// output copy run on three streams, so copies of one chunk overlap the kernel of another.
+// Host-buffer path: the offset-sorted block list is cut into chunks of up to about
+// kHostChunkCoefs coefficients (about kMaxHostChunks of them for large lists, plus short ramp
+// chunks at both ends); chunk c's input copy, kernel and output copy run on three streams, so
+// copies of one chunk overlap the kernel and copies of others.
 constexpr int64_t kHostChunkCoefs = 4 << 20;
 constexpr int kMaxHostChunks = 16;
 struct HostChunk {
@@ -604,9 +605,15 @@ namespace {
 int build_host_chunks(adj_plan* p) {
   free_chunks(p);
   const size_t n = p->blocks.size();
-  const int64_t target = std::max<int64_t>(kHostChunkCoefs, (p->total + kMaxHostChunks - 1) / kMaxHostChunks);
+  const int64_t full = std::max<int64_t>(kHostChunkCoefs, (p->total + kMaxHostChunks - 1) / kMaxHostChunks);
+  int64_t left = 0;
+  for (const adj_block_t& b : p->blocks) left += (int64_t)b.w * b.h;
   TileSet ts;
   for (size_t i = 0; i < n;) {
+    // chunks ramp up (1/4, 1/2, 1 of the full size) and down again near the end, so the first
+    // input copy and the last output copy, which nothing overlaps, stay short
+    const int64_t ramp = full >> std::max(0, 2 - (int)p->chunks.size());
+    const int64_t target = std::max<int64_t>(full / 4, std::min({full, ramp, left / 2}));
     size_t j = i;
     int64_t coefs = 0;
     while (j < n && (j == i || coefs < target)) {
@@ -622,6 +629,7 @@ int build_host_chunks(adj_plan* p) {
     c.n_tiles = (int)ts.tiles.size() - c.tile0;
     c.n_ranges = ts.n_ranges;
     p->chunks.push_back(c);
+    left -= coefs;
     i = j;
   }
   if (!ts.tiles.empty()) {

@@ -129,130 +129,140 @@ __device__ __forceinline__ void q_quad(const float* P, const TfDev& tf, int i, i
   q[2] = make_float2(b.x, b.y); q[3] = make_float2(b.z, b.w);
 }
 
-// One line per thread (T = float): the K-long dot products run in packed FP32x2 along the
-// inputs, {acc_even, acc_odd} += {Q[i][j], Q[i][j+1]} * {v_j, v_{j+1}}, which halves the FMA
-// instructions; the two halves are added at the end of each row.
-template <int N, int KT, class Dst>
-__device__ __forceinline__ void post_fwd_k1(const float (&v)[N], const TfDev& tf, const float* __restrict__ P,
-                                            const Dst& dst) {
-  constexpr int R = PostRows<KT, float>::R;
+// One row of the padded Q in registers.  T = float (one line per thread): row i as KT/4
+// float4; T = float2 (packed line pairs): row i of the duplicated table, {q, q} per entry,
+// KT/2 float4.  get(g, e) is entry 4g + e as the element type.
+template <int KT, class T>
+struct QRow {
+  static constexpr int NQ = sizeof(T) == 4 ? KT / 4 : KT / 2;
+  float4 q[NQ];
+  __device__ __forceinline__ void load(const float* __restrict__ P, const TfDev& tf, int i) {
+    const float4* base = sizeof(T) == 4 ? reinterpret_cast<const float4*>(P + tf.q_off + i * tf.kt)
+                                        : reinterpret_cast<const float4*>(P + tf.q2_off + 2 * i * tf.kt);
 #pragma unroll
-  for (int i = KT; i < N; ++i) dst.put(i, v[i]);
-#pragma unroll 1
-  for (int i = 0; i < KT; i += R) {
-    float2 acc[R][2];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int g = 0; g < KT / 4; ++g) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float q[4];
-        q_quad(P, tf, i + r, g, q);
-        acc[r][0] = __ffma2_rn(make_float2(q[0], q[1]), make_float2(v[4 * g], v[4 * g + 1]), acc[r][0]);
-        acc[r][1] = __ffma2_rn(make_float2(q[2], q[3]), make_float2(v[4 * g + 2], v[4 * g + 3]), acc[r][1]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float2 t = __fadd2_rn(acc[r][0], acc[r][1]);
-      dst.put_rt(i + r, t.x + t.y);
-    }
+    for (int g = 0; g < NQ; ++g) q[g] = __ldg(base + g);
   }
+};
+
+// Forward row: y_i = sum_j Q[i][j] v_j.  One line per thread: packed FP32x2 along the inputs,
+// {acc_even, acc_odd} += {Q[i][j], Q[i][j+1]} * {v_j, v_{j+1}}, halves added at the end.
+// Packed line pairs: one FP32x2 FMA per entry with four partial sums.
+template <int KT, int N>
+__device__ __forceinline__ float post_row(const QRow<KT, float>& r, const float (&v)[N]) {
+  float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int g = 0; g < KT / 4; ++g) {
+    acc0 = __ffma2_rn(make_float2(r.q[g].x, r.q[g].y), make_float2(v[4 * g], v[4 * g + 1]), acc0);
+    acc1 = __ffma2_rn(make_float2(r.q[g].z, r.q[g].w), make_float2(v[4 * g + 2], v[4 * g + 3]), acc1);
+  }
+  const float2 t = __fadd2_rn(acc0, acc1);
+  return t.x + t.y;
 }
+template <int KT, int N>
+__device__ __forceinline__ float2 post_row(const QRow<KT, float2>& r, const float2 (&v)[N]) {
+  float2 acc[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc[e] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int g = 0; g < KT / 4; ++g) {
+    const float4 a = r.q[2 * g], b = r.q[2 * g + 1];
+    acc[0] = __ffma2_rn(make_float2(a.x, a.y), v[4 * g], acc[0]);
+    acc[1] = __ffma2_rn(make_float2(a.z, a.w), v[4 * g + 1], acc[1]);
+    acc[2] = __ffma2_rn(make_float2(b.x, b.y), v[4 * g + 2], acc[2]);
+    acc[3] = __ffma2_rn(make_float2(b.z, b.w), v[4 * g + 3], acc[3]);
+  }
+  return __fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3]));
+}
+
+// Software pipelined over rows when two rows fit in registers (at most 8 float4 each): row
+// i + 1's Q loads are in flight while row i is summed.
+template <int KT, class T>
+constexpr bool kPipeQ = QRow<KT, T>::NQ <= 8;
 
 template <int N, int KT, class T, class Dst>
 __device__ __forceinline__ void post_fwd_k(const T (&v)[N], const TfDev& tf, const float* __restrict__ P,
                                            const Dst& dst) {
-  if constexpr (sizeof(T) == 4) {
-    post_fwd_k1<N, KT>(v, tf, P, dst);
-    return;
-  }
-  constexpr int R = PostRows<KT, T>::R;
 #pragma unroll
   for (int i = KT; i < N; ++i) dst.put(i, v[i]);
+  if constexpr (kPipeQ<KT, T>) {
+    QRow<KT, T> qa, qb;
+    qa.load(P, tf, 0);
 #pragma unroll 1
-  for (int i = 0; i < KT; i += R) {
-    // four partial sums per row (one per position in a Q quad): dependency chains of KT/4
-    T acc[R][4];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[r][e] = vzero(v[0]);
-#pragma unroll
-    for (int g = 0; g < KT / 4; ++g) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        T q[4];
-        q_quad(P, tf, i + r, g, q);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[r][e] = vfma(q[e], v[4 * g + e], acc[r][e]);
-      }
+    for (int i = 0; i < KT; i += 2) {
+      qb.load(P, tf, i + 1);
+      dst.put_rt(i, post_row<KT>(qa, v));
+      if (i + 2 < KT) qa.load(P, tf, i + 2);
+      dst.put_rt(i + 1, post_row<KT>(qb, v));
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) dst.put_rt(i + r, vadd(vadd(acc[r][0], acc[r][1]), vadd(acc[r][2], acc[r][3])));
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < KT; ++i) {
+      QRow<KT, T> q;
+      q.load(P, tf, i);
+      dst.put_rt(i, post_row<KT>(q, v));
+    }
   }
 }
 
-// One line per thread: u_j = sum_i Q[i][j] y_i accumulated as pairs {u_j, u_{j+1}} in packed
-// FP32x2, with y_i broadcast to both halves.
-template <int N, int KT, class Src>
-__device__ __forceinline__ void post_inv_k1(float (&v)[N], const TfDev& tf, const float* __restrict__ P,
-                                            const Src& src) {
-  constexpr int R = PostRows<KT, float>::R;
-  float2 u[KT / 2];
+// Inverse: u_j = sum_i Q[i][j] y_i, y_i read back from the source line.  One line per thread:
+// pairs {u_j, u_{j+1}} in packed FP32x2 with y_i broadcast; packed line pairs: one FP32x2 FMA
+// per entry.  Pipelined over rows like the forward.
+template <int KT, class Src>
+__device__ __forceinline__ void post_inv_row(const QRow<KT, float>& r, const Src& src, int i, float2 (&u)[KT / 2]) {
+  const float t = src.get_rt(i);
+  const float2 y = make_float2(t, t);
 #pragma unroll
-  for (int m = 0; m < KT / 2; ++m) u[m] = make_float2(0.f, 0.f);
-#pragma unroll 1
-  for (int i = 0; i < KT; i += R) {
-    float2 y[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float t = src.get_rt(i + r);
-      y[r] = make_float2(t, t);
-    }
-#pragma unroll
-    for (int g = 0; g < KT / 4; ++g) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float q[4];
-        q_quad(P, tf, i + r, g, q);
-        u[2 * g] = __ffma2_rn(make_float2(q[0], q[1]), y[r], u[2 * g]);
-        u[2 * g + 1] = __ffma2_rn(make_float2(q[2], q[3]), y[r], u[2 * g + 1]);
-      }
-    }
+  for (int g = 0; g < KT / 4; ++g) {
+    u[2 * g] = __ffma2_rn(make_float2(r.q[g].x, r.q[g].y), y, u[2 * g]);
+    u[2 * g + 1] = __ffma2_rn(make_float2(r.q[g].z, r.q[g].w), y, u[2 * g + 1]);
   }
+}
+template <int KT, class Src>
+__device__ __forceinline__ void post_inv_row(const QRow<KT, float2>& r, const Src& src, int i, float2 (&u)[KT]) {
+  const float2 y = src.get_rt(i);
 #pragma unroll
-  for (int m = 0; m < KT / 2; ++m) {
-    v[2 * m] = u[m].x;
-    v[2 * m + 1] = u[m].y;
+  for (int g = 0; g < KT / 4; ++g) {
+    const float4 a = r.q[2 * g], b = r.q[2 * g + 1];
+    u[4 * g] = __ffma2_rn(make_float2(a.x, a.y), y, u[4 * g]);
+    u[4 * g + 1] = __ffma2_rn(make_float2(a.z, a.w), y, u[4 * g + 1]);
+    u[4 * g + 2] = __ffma2_rn(make_float2(b.x, b.y), y, u[4 * g + 2]);
+    u[4 * g + 3] = __ffma2_rn(make_float2(b.z, b.w), y, u[4 * g + 3]);
   }
 }
 
 template <int N, int KT, class T, class Src>
 __device__ __forceinline__ void post_inv_k(T (&v)[N], const TfDev& tf, const float* __restrict__ P, const Src& src) {
-  if constexpr (sizeof(T) == 4) {
-    post_inv_k1<N, KT>(v, tf, P, src);
-    return;
-  }
-  constexpr int R = PostRows<KT, T>::R;
+  constexpr int NU = sizeof(T) == 4 ? KT / 2 : KT;
+  float2 u[NU];
 #pragma unroll
-  for (int j = 0; j < KT; ++j) v[j] = vzero(v[0]);
+  for (int m = 0; m < NU; ++m) u[m] = make_float2(0.f, 0.f);
+  if constexpr (kPipeQ<KT, T>) {
+    QRow<KT, T> qa, qb;
+    qa.load(P, tf, 0);
 #pragma unroll 1
-  for (int i = 0; i < KT; i += R) {
-    T y[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) y[r] = src.get_rt(i + r);
-#pragma unroll
-    for (int g = 0; g < KT / 4; ++g) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        T q[4];
-        q_quad(P, tf, i + r, g, q);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) v[4 * g + e] = vfma(q[e], y[r], v[4 * g + e]);
-      }
+    for (int i = 0; i < KT; i += 2) {
+      qb.load(P, tf, i + 1);
+      post_inv_row<KT>(qa, src, i, u);
+      if (i + 2 < KT) qa.load(P, tf, i + 2);
+      post_inv_row<KT>(qb, src, i + 1, u);
     }
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < KT; ++i) {
+      QRow<KT, T> q;
+      q.load(P, tf, i);
+      post_inv_row<KT>(q, src, i, u);
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int m = 0; m < KT / 2; ++m) {
+      v[2 * m] = u[m].x;
+      v[2 * m + 1] = u[m].y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < KT; ++j) v[j] = u[j];
   }
 }
 
@@ -373,16 +383,17 @@ struct ColSw2 {
 };
 
 // Columns c and c + 1 (c even) of an output block in global memory: 8-byte stores, element i
-// at p + i * S.
+// at p + i * S.  Every output store is a streaming store (evict first): outputs are written
+// once, and keeping them out of L1 leaves it to the transform parameters.
 template <int S>
 struct DstGCol2 {
   float* p;
-  __device__ __forceinline__ void put(int i, float2 x) const { *reinterpret_cast<float2*>(p + i * S) = x; }
-  __device__ __forceinline__ void put_rt(int i, float2 x) const { *reinterpret_cast<float2*>(p + i * S) = x; }
+  __device__ __forceinline__ void put(int i, float2 x) const { __stcs(reinterpret_cast<float2*>(p + i * S), x); }
+  __device__ __forceinline__ void put_rt(int i, float2 x) const { __stcs(reinterpret_cast<float2*>(p + i * S), x); }
   template <int N>
   __device__ __forceinline__ void store(const float2 (&v)[N]) const {
 #pragma unroll
-    for (int i = 0; i < N; ++i) *reinterpret_cast<float2*>(p + i * S) = v[i];
+    for (int i = 0; i < N; ++i) __stcs(reinterpret_cast<float2*>(p + i * S), v[i]);
   }
 };
 
@@ -396,41 +407,41 @@ __device__ __forceinline__ short sat16(float x) {
 struct DstFrame {
   float* p;
   int s;
-  __device__ __forceinline__ void put(int i, float x) const { p[(size_t)i * s] = x; }
-  __device__ __forceinline__ void put_rt(int i, float x) const { p[(size_t)i * s] = x; }
+  __device__ __forceinline__ void put(int i, float x) const { __stcs(p + (size_t)i * s, x); }
+  __device__ __forceinline__ void put_rt(int i, float x) const { __stcs(p + (size_t)i * s, x); }
   template <int N>
   __device__ __forceinline__ void store(const float (&v)[N]) const {
 #pragma unroll
-    for (int i = 0; i < N; ++i) p[(size_t)i * s] = v[i];
+    for (int i = 0; i < N; ++i) __stcs(p + (size_t)i * s, v[i]);
   }
 };
 struct DstFrame2 {
   float* p;
   int s;
-  __device__ __forceinline__ void put(int i, float2 x) const { *reinterpret_cast<float2*>(p + (size_t)i * s) = x; }
-  __device__ __forceinline__ void put_rt(int i, float2 x) const { *reinterpret_cast<float2*>(p + (size_t)i * s) = x; }
+  __device__ __forceinline__ void put(int i, float2 x) const { __stcs(reinterpret_cast<float2*>(p + (size_t)i * s), x); }
+  __device__ __forceinline__ void put_rt(int i, float2 x) const { __stcs(reinterpret_cast<float2*>(p + (size_t)i * s), x); }
   template <int N>
   __device__ __forceinline__ void store(const float2 (&v)[N]) const {
 #pragma unroll
-    for (int i = 0; i < N; ++i) *reinterpret_cast<float2*>(p + (size_t)i * s) = v[i];
+    for (int i = 0; i < N; ++i) __stcs(reinterpret_cast<float2*>(p + (size_t)i * s), v[i]);
   }
 };
 struct DstFrameI16 {
   short* p;
   int s;
-  __device__ __forceinline__ void put(int i, float x) const { p[(size_t)i * s] = sat16(x); }
-  __device__ __forceinline__ void put_rt(int i, float x) const { p[(size_t)i * s] = sat16(x); }
+  __device__ __forceinline__ void put(int i, float x) const { __stcs(p + (size_t)i * s, sat16(x)); }
+  __device__ __forceinline__ void put_rt(int i, float x) const { __stcs(p + (size_t)i * s, sat16(x)); }
   template <int N>
   __device__ __forceinline__ void store(const float (&v)[N]) const {
 #pragma unroll
-    for (int i = 0; i < N; ++i) p[(size_t)i * s] = sat16(v[i]);
+    for (int i = 0; i < N; ++i) __stcs(p + (size_t)i * s, sat16(v[i]));
   }
 };
 struct DstFrameI16x2 {
   short* p;
   int s;
   __device__ __forceinline__ void put(int i, float2 x) const {
-    *reinterpret_cast<short2*>(p + (size_t)i * s) = make_short2(sat16(x.x), sat16(x.y));
+    __stcs(reinterpret_cast<short2*>(p + (size_t)i * s), make_short2(sat16(x.x), sat16(x.y)));
   }
   __device__ __forceinline__ void put_rt(int i, float2 x) const { put(i, x); }
   template <int N>
@@ -444,12 +455,12 @@ struct DstFrameI16x2 {
 template <int S>
 struct DstGCol {
   float* p;
-  __device__ __forceinline__ void put(int i, float x) const { p[i * S] = x; }
-  __device__ __forceinline__ void put_rt(int i, float x) const { p[i * S] = x; }
+  __device__ __forceinline__ void put(int i, float x) const { __stcs(p + i * S, x); }
+  __device__ __forceinline__ void put_rt(int i, float x) const { __stcs(p + i * S, x); }
   template <int N>
   __device__ __forceinline__ void store(const float (&v)[N]) const {
 #pragma unroll
-    for (int i = 0; i < N; ++i) p[i * S] = v[i];
+    for (int i = 0; i < N; ++i) __stcs(p + i * S, v[i]);
   }
 };
 

@@ -282,8 +282,8 @@ __device__ __forceinline__ void multi_col_dct(const TfDev& tv, const float* __re
       float* r0 = side + (size_t)sSide[b] * 4 + (c - kh);
       float* r1 = r0 + kv * wr;
       split_post<H>(v, tv, P, kv, [&](int i, float s7, float c8) {
-        r0[i * wr] = s7;
-        r1[i * wr] = c8;
+        __stcs(r0 + i * wr, s7);
+        __stcs(r1 + i * wr, c8);
       });
     }
   }
@@ -337,13 +337,13 @@ __device__ __forceinline__ void multi_col_adj(const TfDev& tv, const float* __re
     float* lb = sb + L.l(hb) + j;  // row i >= kv of L_b at lb[(i - kv) * kh]
 #pragma unroll
     for (int i = 0; i < H; ++i)
-      if (i >= kv) lb[(i - kv) * kh] = v[i];
+      if (i >= kv) __stcs(lb + (i - kv) * kh, v[i]);
     if (kv > 0) {
       float* x0 = sb + L.x(0, hb) + j;
       float* x1 = sb + L.x(1, hb) + j;
       split_post<H>(v, tv, P, kv, [&](int i, float s7, float c8) {
-        x0[i * kh] = s7;
-        x1[i * kh] = c8;
+        __stcs(x0 + i * kh, s7);
+        __stcs(x1 + i * kh, c8);
       });
     }
   }
