@@ -106,6 +106,17 @@ def test_band_layer_structures(parities):
     full_check(make_workload(tfs, sizes, seed=len(parities)))
 
 
+@pytest.mark.parametrize("parities,lim", [([0, 1] * 32, 0.5), ([0, 1] * 32, 1.0), ([1, 0] * 6, 1.0),
+                                          ([0, 1, 0, 1], 1.04)])
+def test_band_angle_ranges_and_depths(parities, lim):
+    """Deep bands (64 layers) and shallow ones with angles up to 0.5 and 1 rad, every size and
+    a random core per size."""
+    rng = np.random.default_rng(int(lim * 100) + len(parities))
+    tfs = [synth.random_band(rng, n, int(rng.integers(4)), parities, -lim, lim) for n in synth.SIZES]
+    sizes = [(w, h, i, j) for i, w in enumerate(synth.SIZES) for j, h in enumerate(synth.SIZES)] * 3
+    full_check(make_workload(tfs, sizes, seed=len(parities)))
+
+
 @pytest.mark.parametrize("w,h", [(4, 4), (8, 16), (16, 4), (32, 32), (64, 64), (64, 4), (4, 64)])
 def test_tile_capacity_boundaries(w, h):
     cap = _tile_capacity(w, h)
