@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--frames", type=int, default=8, help="frames of the workload (profiling uses fewer)")
+    p.add_argument("--autotune", type=int, default=48, help="autotuner evaluations before timing (0: off)")
     p.add_argument("--no-multiple", action="store_true", help="skip the Multiple-forward measurement")
     p.add_argument("--config5", dest="config5", action="store_true", default=True,
                    help="measure the large-frame workload (default)")
@@ -436,25 +437,33 @@ def run_fused(args):
     coefs = wl.total
     plan = adj.Plan(wl.tfs)
     plan.set_blocks(wl.blocks, coefs)
-    info = plan.info()
     stream = torch.cuda.current_stream(dev)
 
     x = torch.from_numpy(wl.data).to(dev)
     y = torch.empty(coefs, dtype=torch.float32, device=dev)
     xr = torch.empty(coefs, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # the planner's autotuner (tile capacity per block size, CTAs and ranges per SM), then one
+    # CUDA graph per direction around the persistent launch
+    if args.autotune > 0:
+        plan.autotune(x, y, xr, None, args.autotune, stream)
+    tuning = plan.tuning()
+    info = plan.info()
+    from paper_2505_23618_gb300 import _lib as L
+    g_fwd_fused = plan.graph(L.GRAPH_FWD, x, y)
+    g_inv_fused = plan.graph(L.GRAPH_INV, y, xr)
 
     def step(ev=None):
         flush.fill_(1.0)
         if ev:
             ev[0].record(stream)
-        plan.fwd(x, y, stream)
+        g_fwd_fused.launch(stream)
         if ev:
             ev[1].record(stream)
         flush.fill_(2.0)
         if ev:
             ev[2].record(stream)
-        plan.inv(y, xr, stream)
+        g_inv_fused.launch(stream)
         if ev:
             ev[3].record(stream)
 
@@ -481,7 +490,6 @@ def run_fused(args):
 
     # the plain (unfused) form on the same blocks, replayed from CUDA graphs (its best case:
     # no per-launch host overhead); same flushes and event timing as the fused kernels
-    from paper_2505_23618_gb300 import _lib as L
     yp = torch.empty_like(y)
     xrp = torch.empty_like(xr)
     g_fwd = plan.graph(L.GRAPH_FWD_PLAIN, x, yp)
@@ -552,6 +560,11 @@ def run_fused(args):
             "data": "synthetic",
             "config": {"workload": wl.name, "coefs_per_gpu": coefs, "blocks_per_gpu": nb,
                        "tiles": info["n_tiles"], "grid": info["grid_fwd"], "threads": info["threads"],
+                       "tuning": {"autotune_evals": args.autotune, "ctas_per_sm": tuning["ctas_per_sm"],
+                                  "ranges_per_sm": tuning["ranges_per_sm"],
+                                  "cap_div": {f"{4 << (i // 5)}x{4 << (i % 5)}": d
+                                              for i, d in enumerate(tuning["cap_div"]) if d != 1}},
+                       "launch": "one CUDA graph per direction around the persistent kernel",
                        "l2": "flushed by a 256 MiB write before every timed kernel",
                        "layout": "packed block-linear int16 in, FP32 coefficients / reconstruction out"},
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": coefs * (2 + 4),
@@ -574,6 +587,8 @@ def run_fused(args):
         if not args.no_cpu_baseline and world == 1 and args.frames == 8:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
+    g_fwd_fused.close()
+    g_inv_fused.close()
     plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()

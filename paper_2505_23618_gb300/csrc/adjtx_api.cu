@@ -449,11 +449,31 @@ struct TileSet {
   int n_ranges = 0;
 };
 
+// Estimated run time of a tile in the fused kernel (microseconds on GB300 at 6 CTAs per SM),
+// a least-squares fit of measured tile times on a mixed workload: a fixed cost per tile;
+// per line, an extra cost for 64-sample lines (one line per thread, no packed pairs) and for
+// 4-sample rows; and the band rotations (n x layers per line) and post-block products (kt^2
+// per line) of each direction.  The fast cores, loads and stores of shorter lines cost about
+// the same per sample and fold into the fixed part.  Per-SM ranges are balanced on this
+// cost, so that every SM runs out of its own tiles at about the same time.
+double tile_cost(const adj_plan* p, const TileDev& t) {
+  auto adjust = [](const TfHost& f) {
+    if (f.kind == KIND_BAND) return 1.3e-4 * f.n * f.n_layers;
+    if (f.kind == KIND_POST || f.kind == KIND_DENSE) return 1.0e-4 * f.kt * f.kt;
+    return 0.0;
+  };
+  auto row = [&](const TfHost& f) { return (f.n == 64 ? 0.018 : f.n == 4 ? 0.0045 : 0.0) + adjust(f); };
+  auto col = [&](const TfHost& f) { return (f.n == 64 ? 0.021 : 0.0) + adjust(f); };
+  const double lines_h = (double)t.nblk * t.h, lines_v = (double)t.nblk * t.w;
+  return 6.3 + lines_h * row(p->tfs[t.tf_h]) + lines_v * col(p->tfs[t.tf_v]);
+}
+
 // Tiles of the blocks [i0, i1) of the plan's (offset-sorted) list: blocks of one
 // (w, h, tf_h, tf_v) class, filled in storage order, then listed class by class so that
 // consecutive tiles run the same code (by block size, then by the code-determining
 // (core, kind) of each direction, then by transform index); then per-SM ranges of about
-// equal numbers of coefficients.  Block offsets are appended to ts->tblk (4-aligned lists).
+// equal estimated cost (tile_cost), each ordered most expensive tile first.  Block offsets
+// are appended to ts->tblk (4-aligned lists).
 void build_tiles(const adj_plan* p, size_t i0, size_t i1, TileSet* ts) {
   struct Open {
     std::vector<uint32_t> offs, sides;
@@ -526,24 +546,28 @@ void build_tiles(const adj_plan* p, size_t i0, size_t i1, TileSet* ts) {
   if (p->multi || p->frame) tside.resize(tblk.size(), 0u);
 
   // Per-SM ranges of this set's tiles (indices relative to its first tile) with about
-  // equal numbers of coefficients.
+  // equal estimated cost.
   const size_t nt = tiles.size() - first_tile;
   const int n_ranges = nt == 0 ? 0 : (int)std::min<size_t>({(size_t)std::max(1, p->n_sm * std::max(1, p->tuning.ranges_per_sm)), (size_t)kMaxRanges, nt});
   std::vector<unsigned>& rbeg = ts->rbeg;
+  const size_t r0 = rbeg.size();  // this set's first range entry (ts may hold earlier sets)
   if (n_ranges > 0) {
-    std::vector<int64_t> cum(nt + 1, 0);
-    for (size_t i = 0; i < nt; ++i) {
-      const TileDev& t = tiles[first_tile + i];
-      cum[i + 1] = cum[i] + (int64_t)t.nblk * t.w * t.h;
-    }
+    std::vector<double> cum(nt + 1, 0.0);
+    for (size_t i = 0; i < nt; ++i) cum[i + 1] = cum[i] + tile_cost(p, tiles[first_tile + i]);
     rbeg.push_back(0);
     for (int r = 1; r < n_ranges; ++r) {
-      const int64_t target = cum.back() * r / n_ranges;
+      const double target = cum.back() * r / n_ranges;
       size_t i = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
       i = std::max<size_t>(i, rbeg.back());
       rbeg.push_back((unsigned)std::min(i, nt));
     }
     rbeg.push_back((unsigned)nt);
+  }
+  // Within each range the most expensive tiles go first (ties keep the class order), so the
+  // tiles still queued when the ranges run dry are the short ones.
+  for (int r = 0; r < n_ranges; ++r) {
+    auto b = tiles.begin() + first_tile + rbeg[r0 + r], e = tiles.begin() + first_tile + rbeg[r0 + r + 1];
+    std::stable_sort(b, e, [&](const TileDev& x, const TileDev& y) { return tile_cost(p, x) > tile_cost(p, y); });
   }
   ts->n_ranges = n_ranges;
 }
