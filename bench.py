@@ -93,6 +93,42 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# FP32 peak of the ALU roofline: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Flops of one line through a fast core of length N (butterflies 2 flops, rotations 6: the
+# operation counts of the generated core graphs).
+CORE_LINE_FLOPS = {4: 16, 8: 46, 16: 120, 32: 302, 64: 740}
+
+
+def line_flops(tf):
+    """Algorithmic flops of one length-n line through H = C B A (same for the inverse): the fast
+    core, 6 per band rotation, 2 K^2 for the K x K post block; 2 n^2 for the dense kind."""
+    import synth
+    if tf.kind == synth.KIND_DENSE:
+        return 2 * tf.n * tf.n
+    f = CORE_LINE_FLOPS[tf.n]
+    if tf.kind == synth.KIND_BAND:
+        f += 6 * len(tf.angles)
+    elif tf.kind == synth.KIND_POST:
+        f += 2 * tf.q.shape[0] ** 2
+    return f
+
+
+def alg_flops(blocks, tfs):
+    """Algorithmic flops of one 2-D forward (or inverse) over a block list: h rows through the
+    horizontal transform and w columns through the vertical one per block."""
+    import numpy as np
+    lf = np.array([line_flops(t) for t in tfs], dtype=np.float64)
+    return float(np.sum(blocks["h"].astype(np.float64) * lf[blocks["tf_h"]] +
+                        blocks["w"].astype(np.float64) * lf[blocks["tf_v"]]))
+
+
+def alu_roofline(flops, ms):
+    tflops = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": round(tflops, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+            "frac": round(tflops / FP32_PEAK_TFLOPS, 4)}
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2505_23618_gb300", "csrc")
@@ -359,9 +395,11 @@ def bench_config5(args, rank, dev, stream, flush, peak):
         rt = float((xr - x.float()).abs().max())
     meta = tiles * 16 + nb * 4
     bf, bi = coefs * 6 + meta, coefs * 8 + meta
+    fl = alg_flops(wl.blocks, wl.tfs)
     out.update({"value": round(coefs / ((tf + ti) * 1e-3) / 1e9, 3), "unit": UNIT, "coefs": coefs,
                 "fwd_ms": round(tf, 4), "inv_ms": round(ti, 4),
                 "fwd_frac": round(bf / (tf * 1e-3) / 1e9 / peak, 4), "inv_frac": round(bi / (ti * 1e-3) / 1e9 / peak, 4),
+                "flops_per_coef": round(fl / coefs, 2), "alu_fwd": alu_roofline(fl, tf), "alu_inv": alu_roofline(fl, ti),
                 "roundtrip_max_abs_err": rt})
     # the exact transforms the adjustments stand in for, as dense products (Eq. 3)
     dense = [targets.dense_tf(targets.dst7(64)), targets.dense_tf(targets.dct8(64)), targets.dense_tf(targets.dct8(32))]
@@ -536,6 +574,7 @@ def run_fused(args):
     e2e_t = aggregate_max((time.perf_counter() - t0) / args.e2e_steps, dev)
     e2e_value = whole_job_rate(coefs, world, 1, e2e_t) / 1e9
 
+    flops = alg_flops(wl.blocks, wl.tfs)  # per launch, forward or inverse
     # roofline of the dominant kernel (algorithmic bytes per launch / mean duration)
     nb = int(wl.blocks.size)
     meta = info["n_tiles"] * 16 + nb * 4
@@ -581,6 +620,8 @@ def run_fused(args):
             "frame": frame,
             "kernels": {k: {"ms": round(v["ms"], 4), "GB/s": round(v["gbs"], 1), "frac": round(v["frac"], 4)}
                         for k, v in kern.items()},
+            "flops_per_coef": round(flops / coefs, 2),
+            "alu_roofline": {k: alu_roofline(flops, v["ms"]) for k, v in kern.items()},
             "clocks": clk.summary(),
             "roundtrip_max_abs_err": rt,
         }

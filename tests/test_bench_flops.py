@@ -1,0 +1,45 @@
+"""The bench's algorithmic flop counts (ALU roofline): the per-line core counts agree with the
+operation counts the generator wrote for every core graph, and a block list sums by hand."""
+
+import os
+import re
+
+import numpy as np
+
+import bench
+import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CORES = os.path.join(HERE, "..", "paper_2505_23618_gb300", "csrc", "cores_gen.cuh")
+
+
+def test_core_line_flops_match_the_generated_graphs():
+    pat = re.compile(r"^// (DCT2|DCT3|DST2|DST3) N=(\d+): (\d+) butterflies \(2 FADD\), (\d+) rotations")
+    seen = set()
+    with open(CORES) as f:
+        for ln in f:
+            m = pat.match(ln)
+            if m:
+                n, bfly, rot = int(m.group(2)), int(m.group(3)), int(m.group(4))
+                assert bench.CORE_LINE_FLOPS[n] == 2 * bfly + 6 * rot, (m.group(1), n)
+                seen.add((m.group(1), n))
+    assert len(seen) == 20
+
+
+def test_line_and_block_flops():
+    rng = np.random.default_rng(0)
+    band = synth.random_band(rng, 16, 3, [0, 1, 0, 1])          # 8 + 7 + 8 + 7 rotations
+    post = synth.random_post(rng, 8, 0, 4)
+    none = synth.Tf(n=4, core=2)
+    dense = synth.Tf(n=8, core=0, kind=synth.KIND_DENSE, q=np.eye(8))
+    assert bench.line_flops(band) == 120 + 6 * 30
+    assert bench.line_flops(post) == 46 + 2 * 16
+    assert bench.line_flops(none) == 16
+    assert bench.line_flops(dense) == 128
+    tfs = [band, post, none, dense]
+    blocks = np.zeros(2, dtype=synth.BLOCK_DTYPE)
+    blocks["w"], blocks["h"] = (16, 4), (8, 8)
+    blocks["tf_h"], blocks["tf_v"] = (0, 2), (1, 3)
+    # block 0: 8 rows of 16 (band) + 16 columns of 8 (post); block 1: 8 rows of 4 + 4 columns of 8
+    want = 8 * 300 + 16 * 78 + 8 * 16 + 4 * 128
+    assert bench.alg_flops(blocks, tfs) == want
