@@ -146,6 +146,15 @@ int adj_transform_fwd(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, v
 int adj_transform_inv(adj_plan_t* plan, const float* d_coef, float* d_resid_out, void* stream);
 
 /*
+ * Forward 2-D transform of FP32 blocks (Eq. 1 applied to inputs that are not int16
+ * residuals, e.g. the FP32 input of a gradient computation): d_x (FP32, device, total_coefs,
+ * 16-B aligned) -> d_coef as adj_transform_fwd.  Same kernel design with FP32 staging, one
+ * persistent launch, asynchronous on `stream`.  Errors: INVALID_ARG, NO_BLOCKS, MISALIGNED,
+ * CUDA.
+ */
+int adj_transform_fwd_f32(adj_plan_t* plan, const float* d_x, float* d_coef, void* stream);
+
+/*
  * Blocks inside a frame.  The adjustments act on W x B and B x H regions of a frame
  * (Section 2.2); a codec keeps its residual and its reconstruction as frames, so these calls
  * read each block from its place in a residual frame and write it back to its place,

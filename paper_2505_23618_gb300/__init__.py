@@ -8,7 +8,14 @@ library behind the C ABI of include/adjtx.h; this package only marshals argument
 
 from ._lib import (ADJ_OK, BLOCK_DTYPE, ERR_CODE, ERRORS, EXPORTED, LIB_PATH, AdjError,  # noqa: F401
                    Plan, check, lib, load)
-from .torch_api import forward, forward_multiple, inverse, roundtrip  # noqa: F401
+from .torch_api import (adjusted_transform, autograd_function, forward, forward_multiple, inverse,  # noqa: F401
+                        param_vector, roundtrip)
 
-__all__ = ["Plan", "AdjError", "forward", "forward_multiple", "inverse", "roundtrip", "BLOCK_DTYPE", "lib",
-           "LIB_PATH", "EXPORTED"]
+__all__ = ["Plan", "AdjError", "forward", "forward_multiple", "inverse", "roundtrip", "adjusted_transform",
+           "autograd_function", "param_vector", "AdjFn", "BLOCK_DTYPE", "lib", "LIB_PATH", "EXPORTED"]
+
+
+def __getattr__(name):
+    if name == "AdjFn":   # torch.autograd.Function, built on first use
+        return autograd_function()
+    raise AttributeError(name)

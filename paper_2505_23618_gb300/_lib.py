@@ -34,6 +34,7 @@ EXPORTED = (
     "adj_plan_param_layout", "adj_coding_gain_proxy", "adj_plan_get_tuning", "adj_plan_set_tuning",
     "adj_plan_autotune", "adj_plan_prepare_multiple", "adj_transform_fwd_multiple",
     "adj_plan_set_frame_blocks", "adj_transform_fwd_frame", "adj_transform_inv_frame",
+    "adj_transform_fwd_f32",
 )
 DTYPE_INT16, DTYPE_FP32 = 0, 1
 GRAPH_FWD, GRAPH_INV, GRAPH_FWD_PLAIN, GRAPH_INV_PLAIN, GRAPH_ROUNDTRIP, GRAPH_FWD_MULTIPLE = range(6)
@@ -77,8 +78,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.adj_plan_create.argtypes = [C.POINTER(vp), C.POINTER(Adj1dDesc), i32, i32]
     lib.adj_plan_set_blocks.argtypes = [vp, vp, i64, i64]
     lib.adj_plan_update_params.argtypes = [vp, C.POINTER(Adj1dDesc), i32]
-    for f in ("adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host", "adj_transform_inv_host",
-              "adj_transform_fwd_plain", "adj_transform_inv_plain"):
+    for f in ("adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_f32", "adj_transform_fwd_host",
+              "adj_transform_inv_host", "adj_transform_fwd_plain", "adj_transform_inv_plain"):
         getattr(lib, f).argtypes = [vp, vp, vp, vp]
     lib.adj_plan_info.argtypes = [vp, C.POINTER(AdjPlanInfo)]
     lib.adj_transform_fwd_uniform_noalloc.argtypes = [C.POINTER(Adj1dDesc), C.POINTER(Adj1dDesc), i64, vp, vp, vp]
@@ -203,6 +204,10 @@ class Plan:
 
     def inv(self, d_in, d_out, stream=None):
         check(self._lib.adj_transform_inv(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+    def fwd_f32(self, d_in, d_out, stream=None):
+        """Forward of FP32 blocks (adj_transform_fwd_f32)."""
+        check(self._lib.adj_transform_fwd_f32(self._h, _ptr(d_in), _ptr(d_out), _stream(stream)))
 
     def set_frame_blocks(self, blocks: np.ndarray, frame_w: int, frame_h: int, stride: int):
         """Blocks inside a frame (FRAME_BLOCK_DTYPE records); coefficients are packed in list order."""

@@ -107,6 +107,7 @@ struct adj_plan {
   uint32_t* d_tile_side = nullptr;     // side or frame offset / 4, parallel to d_tile_blk
   int occ_multi = 0, grid_multi = 0;
   int occ_frame = 0, grid_frame = 0;
+  int occ_f32 = 0, grid_f32 = 0;      // forward of FP32 blocks
   adj_tuning_t tuning{};
   int occ_fwd = 0, occ_inv = 0;        // resident CTAs per SM of the fused kernels
   // host-buffer path (built on first use, dropped with the block layout)
@@ -302,6 +303,29 @@ int run(adj_plan* p, bool inverse, const void* in, float* out, cudaStream_t stre
   return ADJ_OK;
 }
 
+// Forward of packed FP32 blocks: the fused kernel with FP32 staging, on the forward's tiles.
+int run_fwd_f32(adj_plan* p, const float* in, float* out, cudaStream_t stream) {
+  if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
+  if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
+  int rc;
+  if ((rc = check_ptr(in, "input")) || (rc = check_ptr(out, "output"))) return rc;
+  if (p->n_tiles == 0) return ADJ_OK;
+  FusedArgs a{};
+  a.tiles = p->d_tiles;
+  a.tile_blk = p->d_tile_blk;
+  a.tfs = p->d_tfs;
+  a.params = p->d_params;
+  a.in = in;
+  a.out = out;
+  a.sched = p->d_sched;
+  a.range_begin = p->d_range_begin;
+  a.n_tiles = p->n_tiles;
+  a.n_ranges = p->n_ranges;
+  cudaError_t e = launch_fwd_f32(p->grid_f32, a, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "FP32 forward launch");
+  return ADJ_OK;
+}
+
 int run_multi(adj_plan* p, const int16_t* in, float* out, float* side, cudaStream_t stream) {
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
   if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
@@ -436,6 +460,7 @@ void apply_grid(adj_plan* p) {
   p->grid_inv = std::max(1, c > 0 ? std::min(c, p->occ_inv) : p->occ_inv) * p->n_sm;
   p->grid_multi = std::max(1, c > 0 ? std::min(c, p->occ_multi) : p->occ_multi) * p->n_sm;
   p->grid_frame = std::max(1, c > 0 ? std::min(c, p->occ_frame) : p->occ_frame) * p->n_sm;
+  p->grid_f32 = std::max(1, c > 0 ? std::min(c, p->occ_f32) : p->occ_f32) * p->n_sm;
 }
 
 // Tiles, per-SM ranges and the plain form's per-size lists for the plan's block list,
@@ -866,6 +891,14 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
     else p->occ_multi = std::max(1, occ);
   }
+  if (!rc) {
+    const void* fn = fwd_f32_kernel_ptr();
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
+    if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
+    else p->occ_f32 = std::max(1, occ);
+  }
   for (int v = 0; v < 3 && !rc; ++v) {  // frame forward, inverse FP32, inverse int16
     const void* fn = frame_kernel_ptr(v > 0, v == 2);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -951,6 +984,11 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
 int adj_transform_fwd(adj_plan_t* p, const int16_t* d_resid, float* d_coef, void* stream) {
   g_err.clear();
   return run(p, false, d_resid, d_coef, static_cast<cudaStream_t>(stream));
+}
+
+int adj_transform_fwd_f32(adj_plan_t* p, const float* d_x, float* d_coef, void* stream) {
+  g_err.clear();
+  return run_fwd_f32(p, d_x, d_coef, static_cast<cudaStream_t>(stream));
 }
 
 int adj_transform_inv(adj_plan_t* p, const float* d_coef, float* d_resid_out, void* stream) {

@@ -25,12 +25,13 @@
 
 namespace adjtx {
 
-// Issue the asynchronous copies of one tile's input into a tile buffer (block width W).
-template <int W, bool INV, int THREADS>
+// Issue the asynchronous copies of one tile's input into a tile buffer (block width W):
+// FP32 input (the inverse, and the forward of FP32 blocks) or int16 residuals.
+template <int W, bool F32, int THREADS>
 __device__ __forceinline__ void stage_tile_w(const TileDev& td, const uint32_t* sOff, const void* in, float* buf) {
   constexpr int SH = sw_shift(W), MK = sw_mask(W);
   const int h = td.h, nb = td.nblk, lgh = lg2(h);
-  if constexpr (INV) {
+  if constexpr (F32) {
     // FP32 chunks of 4 samples: W/4 per row
     constexpr int LG_CPR = ilog2(W / 4);
     const int lg_cpb = LG_CPR + lgh, total = nb << lg_cpb;
@@ -113,20 +114,20 @@ __device__ __forceinline__ void stage_frame(const TileDev& td, const uint32_t* s
 
 // MAXN: the largest block side the kernel instance handles (code for longer lines is not
 // instantiated).
-template <bool INV, int THREADS, int MAXN>
+template <bool F32, int THREADS, int MAXN>
 __device__ __forceinline__ void stage_tile(const TileDev& td, const uint32_t* sOff, const void* in, float* buf) {
   switch (td.w) {
-    case 4: stage_tile_w<4, INV, THREADS>(td, sOff, in, buf); break;
-    case 8: stage_tile_w<8, INV, THREADS>(td, sOff, in, buf); break;
-    case 16: stage_tile_w<16, INV, THREADS>(td, sOff, in, buf); break;
-    case 32: if constexpr (MAXN >= 32) { stage_tile_w<32, INV, THREADS>(td, sOff, in, buf); } break;
-    default: if constexpr (MAXN >= 64) { stage_tile_w<64, INV, THREADS>(td, sOff, in, buf); } break;
+    case 4: stage_tile_w<4, F32, THREADS>(td, sOff, in, buf); break;
+    case 8: stage_tile_w<8, F32, THREADS>(td, sOff, in, buf); break;
+    case 16: stage_tile_w<16, F32, THREADS>(td, sOff, in, buf); break;
+    case 32: if constexpr (MAXN >= 32) { stage_tile_w<32, F32, THREADS>(td, sOff, in, buf); } break;
+    default: if constexpr (MAXN >= 64) { stage_tile_w<64, F32, THREADS>(td, sOff, in, buf); } break;
   }
 }
 
 // Lines of at most 32 samples are transformed two at a time (lines l and l + half share a
 // thread, packed FP32x2 arithmetic); 64-sample lines one per thread.
-template <int W, bool INV, int THREADS>
+template <int W, bool INV, int THREADS, bool I16 = !INV>
 __device__ __forceinline__ void row_pass(const TfDev& tf, const float* __restrict__ P, float* buf, int nb, int h) {
   constexpr int SH = sw_shift(W), MK = sw_mask(W);
   const int nlines = nb * h;
@@ -136,13 +137,13 @@ __device__ __forceinline__ void row_pass(const TfDev& tf, const float* __restric
       const int l2 = l + half;
       Pair<RowSw> row{RowSw{buf + l * W, ((l & (h - 1)) >> SH) & MK},
                       RowSw{buf + l2 * W, ((l2 & (h - 1)) >> SH) & MK}};
-      line_transform<W, INV, !INV, float2>(tf, P, row, row);
+      line_transform<W, INV, I16, float2>(tf, P, row, row);
     }
   } else {
     for (int l = threadIdx.x; l < nlines; l += THREADS) {
       const int r = l & (h - 1);
       RowSw row{buf + l * W, (r >> SH) & MK};
-      line_transform<W, INV, !INV>(tf, P, row, row);
+      line_transform<W, INV, I16>(tf, P, row, row);
     }
   }
 }
@@ -397,9 +398,11 @@ __global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kern
   constexpr bool MULTI = MODE == kModeMulti;
   constexpr bool FRAME_IN = !INV && MODE == kModeFrame;   // forward reading blocks from a frame
   constexpr int OUT = !INV || MODE < kModeFrame ? 0 : (MODE == kModeFrame ? 1 : 2);
-  constexpr bool AUX = MODE != kModePacked;
+  constexpr bool AUX = MODE == kModeMulti || MODE == kModeFrame || MODE == kModeFrameI16;
+  constexpr bool F32_IN = INV || MODE == kModePackedF32;  // staged input is FP32 (else int16)
   static_assert(!(INV && MULTI), "the Multiple form is forward only");
   static_assert(MAXN == 64 || MODE == kModePacked, "short-line instances are for packed blocks");
+  static_assert(!(INV && MODE == kModePackedF32), "FP32 input is the inverse's own");
   static_assert(INV || MODE != kModeFrameI16, "int16 output is for the inverse");
   extern __shared__ __align__(16) unsigned char smem[];
   // Records of this CTA's tiles, by the tile's sequence number k in the CTA:
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kern
     if constexpr (FRAME_IN) {
       stage_frame<THREADS>(d0, sAux[0] + (d0.blk_begin & 3), a.in, a.frame_stride, reinterpret_cast<float*>(smem));
     } else {
-      stage_tile<INV, THREADS, MAXN>(d0, sOff[0] + (d0.blk_begin & 3), a.in, reinterpret_cast<float*>(smem));
+      stage_tile<F32_IN, THREADS, MAXN>(d0, sOff[0] + (d0.blk_begin & 3), a.in, reinterpret_cast<float*>(smem));
     }
     if (tn >= 0) {
       const TileDev d1 = a.tiles[tn];
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kern
       if constexpr (FRAME_IN) {
         stage_frame<THREADS>(dn, sAux[(k + 1) % 3] + (dn.blk_begin & 3), a.in, a.frame_stride, nbuf);
       } else {
-        stage_tile<INV, THREADS, MAXN>(dn, sOff[(k + 1) % 3] + (dn.blk_begin & 3), a.in, nbuf);
+        stage_tile<F32_IN, THREADS, MAXN>(dn, sOff[(k + 1) % 3] + (dn.blk_begin & 3), a.in, nbuf);
       }
       copy_async<THREADS>(&sTf[cur ^ 1][0], a.tfs + dn.tf_h, sizeof(TfDev));
       copy_async<THREADS>(&sTf[cur ^ 1][1], a.tfs + dn.tf_v, sizeof(TfDev));
@@ -507,11 +510,11 @@ __global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kern
       TfDev tf = sTf[cur][0];
       if constexpr (MULTI) tf.kind = KIND_NONE;  // the rows get the plain DCT-2 first
       switch (w) {
-        case 4: row_pass<4, INV, THREADS>(tf, a.params, buf, nb, h); break;
-        case 8: row_pass<8, INV, THREADS>(tf, a.params, buf, nb, h); break;
-        case 16: row_pass<16, INV, THREADS>(tf, a.params, buf, nb, h); break;
-        case 32: if constexpr (MAXN >= 32) { row_pass<32, INV, THREADS>(tf, a.params, buf, nb, h); } break;
-        default: if constexpr (MAXN >= 64) { row_pass<64, INV, THREADS>(tf, a.params, buf, nb, h); } break;
+        case 4: row_pass<4, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
+        case 8: row_pass<8, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
+        case 16: row_pass<16, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
+        case 32: if constexpr (MAXN >= 32) { row_pass<32, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); } break;
+        default: if constexpr (MAXN >= 64) { row_pass<64, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); } break;
       }
     }
     // (4)

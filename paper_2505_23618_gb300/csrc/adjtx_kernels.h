@@ -27,7 +27,7 @@ struct FusedArgs {
 };
 
 // Kernel modes (template argument of the fused kernel).
-enum { kModePacked = 0, kModeMulti = 1, kModeFrame = 2, kModeFrameI16 = 3 };
+enum { kModePacked = 0, kModeMulti = 1, kModeFrame = 2, kModeFrameI16 = 3, kModePackedF32 = 4 };
 
 // Plain (unfused) form: the blocks of one size class, each with its own transforms.
 struct PlainBlock {
@@ -67,6 +67,9 @@ cudaError_t launch_multi(int grid, const FusedArgs& args, cudaStream_t stream);
 // frame modes: forward reads int16 blocks from a frame; inverse writes FP32 or rounded int16
 const void* frame_kernel_ptr(bool inverse, bool i16);
 cudaError_t launch_frame(bool inverse, bool i16, int grid, const FusedArgs& args, cudaStream_t stream);
+// Forward over packed FP32 input (kModePackedF32), for inputs that are not int16 residuals.
+const void* fwd_f32_kernel_ptr();
+cudaError_t launch_fwd_f32(int grid, const FusedArgs& args, cudaStream_t stream);
 const void* fused_fwd_ptr();
 const void* fused_inv_ptr();
 void set_last_error(const char* msg);

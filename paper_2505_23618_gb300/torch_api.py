@@ -51,3 +51,131 @@ def forward_multiple(plan, resid, side_offsets=None, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream(resid.device)
     plan.fwd_multiple(resid, y, side, s)
     return y, side, side_offsets
+
+
+# ---------------------------------------------------------------------------------------
+# Autograd: the forward transform as a differentiable function of its input and of the
+# adjustment parameters (the design of Section 2.2 fits these parameters, Eq. 2).
+# ---------------------------------------------------------------------------------------
+
+def _layout(plan):
+    lay = getattr(plan, "_param_layout", None)
+    if lay is None:
+        lay = plan.param_layout()
+        plan._param_layout = lay
+    return lay
+
+
+def _field(tf, name, default=None):
+    return tf.get(name, default) if isinstance(tf, dict) else getattr(tf, name, default)
+
+
+def param_vector(plan, dtype=None, device=None):
+    """The plan's parameters in its gradient layout (adj_plan_param_layout): per transform the
+    band angles, the K x K post block Q (row major) or the n x n dense matrix; nothing for a
+    plain core.  Returns a 1-D tensor (FP64 by default, on `device`)."""
+    import numpy as np
+    torch = _torch()
+    lay = _layout(plan)
+    v = np.zeros(lay[-1], dtype=np.float64)
+    for i, tf in enumerate(plan.tfs):
+        kind = int(_field(tf, "kind", 0))
+        if kind == 1:
+            v[lay[i]:lay[i + 1]] = np.asarray(_field(tf, "angles"), dtype=np.float64)
+        elif kind in (2, 3):
+            v[lay[i]:lay[i + 1]] = np.asarray(_field(tf, "q"), dtype=np.float64).ravel()
+    return torch.tensor(v, dtype=dtype or torch.float64, device=device)
+
+
+def _set_params(plan, values):
+    """Upload parameter values given in the gradient layout (host FP64 array); the structure of
+    every transform (n, core, kind, layer parities, K) is kept."""
+    import numpy as np
+    lay = _layout(plan)
+    tfs = []
+    for i, tf in enumerate(plan.tfs):
+        kind = int(_field(tf, "kind", 0))
+        d = {"n": int(_field(tf, "n")), "core": int(_field(tf, "core")), "kind": kind,
+             "parities": _field(tf, "parities", np.zeros(0))}
+        seg = values[lay[i]:lay[i + 1]]
+        if kind == 1:
+            d["angles"] = seg.copy()
+        elif kind in (2, 3):
+            k = int(round(np.sqrt(seg.size)))
+            d["q"] = seg.reshape(k, k).copy()
+        tfs.append(d)
+    plan.update_params(tfs)
+    plan._param_values = values.copy()
+
+
+def _make_autograd():
+    torch = _torch()
+    import numpy as np
+
+    class _AdjFn(torch.autograd.Function):
+        """Y = forward transform of x (int16 or FP32 blocks in the plan's packed layout) under the
+        parameter vector `params` (gradient layout, see param_vector).  The parameters are uploaded
+        to the plan when they differ from its current ones (post blocks must stay orthogonal to
+        1e-6, e.g. through a Cayley map computed in torch).  Backward: adj_transform_bwd gives
+        dL/dx (FP32 inputs) and dL/dparams (band angles, Q entries, dense entries)."""
+
+        @staticmethod
+        def forward(ctx, x, params, plan):
+            vals = params.detach().to("cpu", torch.float64).numpy()
+            cur = getattr(plan, "_param_values", None)
+            if cur is None or cur.shape != vals.shape or not np.array_equal(cur, vals):
+                _set_params(plan, vals)
+            y = torch.zeros(plan.total, dtype=torch.float32, device=x.device)
+            s = torch.cuda.current_stream(x.device)
+            if x.dtype == torch.int16:
+                plan.fwd(x, y, s)
+            elif x.dtype == torch.float32:
+                plan.fwd_f32(x.contiguous(), y, s)
+            else:
+                raise TypeError("x must be a CUDA int16 or float32 tensor")
+            ctx.plan, ctx.vals, ctx.p_dtype = plan, vals, params.dtype
+            ctx.save_for_backward(x)
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            (x,) = ctx.saved_tensors
+            plan = ctx.plan
+            if not np.array_equal(plan._param_values, ctx.vals):
+                _set_params(plan, ctx.vals)
+            need_x, need_p = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+            gx = torch.zeros(plan.total, dtype=torch.float32, device=x.device) if need_x else None
+            n_grad = _layout(plan)[-1]
+            gp = torch.zeros(max(1, n_grad), dtype=torch.float32, device=x.device) if need_p else None
+            if need_x or need_p:
+                plan.bwd(x.contiguous(), gy.contiguous().float(), gx, gp, torch.cuda.current_stream(x.device),
+                         x_fp32=x.dtype == torch.float32)
+            if gp is not None:
+                gp = gp[:n_grad].to(ctx.p_dtype)
+            return gx, gp, None
+
+    return _AdjFn
+
+
+_ADJFN = None
+
+
+def autograd_function():
+    """The torch.autograd.Function of the forward transform (built on first use, so that
+    importing the package does not import torch)."""
+    global _ADJFN
+    if _ADJFN is None:
+        _ADJFN = _make_autograd()
+    return _ADJFN
+
+
+def adjusted_transform(x, params, plan):
+    """Differentiable forward transform: Y(x, params) for the plan's block list;
+    ``AdjFn.apply(x, params, plan)`` with AdjFn = autograd_function()."""
+    return autograd_function().apply(x, params, plan)
+
+
+def __getattr__(name):
+    if name == "AdjFn":
+        return autograd_function()
+    raise AttributeError(name)

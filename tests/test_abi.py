@@ -107,7 +107,8 @@ def test_create_rejects_null_and_counts(lib):
 
 
 def test_null_plan_calls_fail_cleanly(lib):
-    for f in ("adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_host", "adj_transform_inv_host"):
+    for f in ("adj_transform_fwd", "adj_transform_inv", "adj_transform_fwd_f32", "adj_transform_fwd_host",
+              "adj_transform_inv_host"):
         assert getattr(lib, f)(None, None, None, None) == _lib.ERR_CODE["ADJ_ERR_INVALID_ARG"]
     assert lib.adj_plan_set_blocks(None, None, 0, 0) == _lib.ERR_CODE["ADJ_ERR_INVALID_ARG"]
     assert lib.adj_plan_prepare_multiple(None, None, None) == _lib.ERR_CODE["ADJ_ERR_INVALID_ARG"]
