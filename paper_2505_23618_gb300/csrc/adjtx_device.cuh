@@ -53,6 +53,12 @@ __device__ __forceinline__ void load_cs(const float* P, const TfDev& tf, int idx
   s = make_float2(t.z, t.w);
 }
 
+// Negation written per component, so that it folds into the FP32x2 FMA consuming it (one
+// instruction less per rotation than a product with -1).  The inverse keeps the product form:
+// with the folded one its register allocation changed and it ran about 1 % slower.
+__device__ __forceinline__ float rneg(float a) { return -a; }
+__device__ __forceinline__ float2 rneg(float2 a) { return make_float2(-a.x, -a.y); }
+
 template <int N, int PAR, bool INV, class T>
 __device__ __forceinline__ void rot_layer(T (&v)[N], const TfDev& tf, const float* __restrict__ P, int off) {
 #pragma unroll
@@ -62,7 +68,7 @@ __device__ __forceinline__ void rot_layer(T (&v)[N], const TfDev& tf, const floa
     load_cs(P, tf, off + p, c, s);
     const T x = v[i], y = v[i + 1];
     if (!INV) {
-      v[i] = vfma(c, x, vneg(vmulv(s, y)));
+      v[i] = vfma(c, x, rneg(vmulv(s, y)));
       v[i + 1] = vfma(c, y, vmulv(s, x));
     } else {
       v[i] = vfma(c, x, vmulv(s, y));
