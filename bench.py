@@ -52,6 +52,8 @@ def parse():
                    help="measure the large-frame workload (default)")
     p.add_argument("--no-config5", dest="config5", action="store_false")
     p.add_argument("--no-frame", action="store_true", help="skip the frame-layout measurement")
+    p.add_argument("--classes", action="store_true",
+                   help="diagnostic: time uniform single-class workloads (one JSON line per class) instead")
     return p.parse_args()
 
 
@@ -636,10 +638,75 @@ def run_fused(args):
     return 0
 
 
+# Uniform single-class workloads of the diagnostic mode: (w, h, core, kind); band = 2 layers
+# (even, odd), post K = n / 2; about 2^26 coefficients each.
+CLASSES = [(64, 64, 0, 0), (64, 64, 0, 1), (64, 64, 0, 2), (32, 32, 0, 0), (32, 32, 2, 1), (32, 32, 0, 2),
+           (16, 16, 0, 0), (16, 16, 3, 1), (8, 8, 0, 0), (4, 4, 0, 0), (4, 64, 0, 0), (64, 4, 0, 0)]
+
+
+def run_classes(args):
+    """Forward and inverse times of uniform workloads, one block class each (L2 flushed before
+    every timed kernel, CUDA events); a diagnostic of where the mixed workload spends its time."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2505_23618_gb300 as adj
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(0)
+    peak, _ = measured_peak()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def tf(n, core, kind):
+        if kind == synth.KIND_NONE:
+            return synth.Tf(n=n, core=core)
+        if kind == synth.KIND_BAND:
+            return synth.random_band(rng, n, core, [0, 1])
+        return synth.random_post(rng, n, core, n // 2)
+
+    for w, h, core, kind in CLASSES:
+        nb = (1 << 26) // (w * h)
+        blocks = np.zeros(nb, dtype=synth.BLOCK_DTYPE)
+        blocks["offset"] = np.arange(nb, dtype=np.int64) * w * h
+        blocks["w"], blocks["h"], blocks["tf_h"], blocks["tf_v"] = w, h, 0, 1
+        total = nb * w * h
+        x = torch.randint(-500, 500, (total,), dtype=torch.int16, device=dev)
+        y = torch.empty(total, device=dev)
+        xr = torch.empty_like(y)
+        with adj.Plan([tf(w, core, kind), tf(h, core, kind)]) as plan:
+            plan.set_blocks(blocks, total)
+            for _ in range(max(1, args.warmup)):
+                plan.fwd(x, y)
+                plan.inv(y, xr)
+            tf_, ti_ = [], []
+            for _ in range(max(1, args.steps)):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                flush.fill_(1.0)
+                ev[0].record()
+                plan.fwd(x, y)
+                ev[1].record()
+                flush.fill_(2.0)
+                ev[2].record()
+                plan.inv(y, xr)
+                ev[3].record()
+                torch.cuda.synchronize()
+                tf_.append(ev[0].elapsed_time(ev[1]))
+                ti_.append(ev[2].elapsed_time(ev[3]))
+            mf, mi = float(np.median(tf_)), float(np.median(ti_))
+            print(json.dumps({"class": f"{w}x{h} core {core} kind {kind}", "coefs": total, "tiles": plan.info()["n_tiles"],
+                              "fwd_ms": round(mf, 4), "inv_ms": round(mi, 4),
+                              "fwd_frac": round(total * 6 / (mf * 1e-3) / 1e9 / peak, 4),
+                              "inv_frac": round(total * 8 / (mi * 1e-3) / 1e9 / peak, 4)}), flush=True)
+        del x, y, xr
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.classes:
+        return run_classes(args)
     return run_fused(args)
 
 
