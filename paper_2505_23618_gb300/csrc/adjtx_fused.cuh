@@ -112,16 +112,14 @@ __device__ __forceinline__ void stage_frame(const TileDev& td, const uint32_t* s
   }
 }
 
-// MAXN: the largest block side the kernel instance handles (code for longer lines is not
-// instantiated).
-template <bool F32, int THREADS, int MAXN>
+template <bool F32, int THREADS>
 __device__ __forceinline__ void stage_tile(const TileDev& td, const uint32_t* sOff, const void* in, float* buf) {
   switch (td.w) {
     case 4: stage_tile_w<4, F32, THREADS>(td, sOff, in, buf); break;
     case 8: stage_tile_w<8, F32, THREADS>(td, sOff, in, buf); break;
     case 16: stage_tile_w<16, F32, THREADS>(td, sOff, in, buf); break;
-    case 32: if constexpr (MAXN >= 32) { stage_tile_w<32, F32, THREADS>(td, sOff, in, buf); } break;
-    default: if constexpr (MAXN >= 64) { stage_tile_w<64, F32, THREADS>(td, sOff, in, buf); } break;
+    case 32: stage_tile_w<32, F32, THREADS>(td, sOff, in, buf); break;
+    default: stage_tile_w<64, F32, THREADS>(td, sOff, in, buf); break;
   }
 }
 
@@ -187,7 +185,7 @@ __device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restric
   }
 }
 
-template <int H, bool INV, int THREADS, int OUT, int MAXN>
+template <int H, bool INV, int THREADS, int OUT>
 __device__ __forceinline__ void col_dispatch(const TfDev& tf, const float* __restrict__ P, const float* buf,
                                              const uint32_t* sOff, const uint32_t* sAux, float* __restrict__ out,
                                              int nb, int w, int stride) {
@@ -195,8 +193,8 @@ __device__ __forceinline__ void col_dispatch(const TfDev& tf, const float* __res
     case 4: col_pass<H, 4, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
     case 8: col_pass<H, 8, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
     case 16: col_pass<H, 16, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
-    case 32: if constexpr (MAXN >= 32) { col_pass<H, 32, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); } break;
-    default: if constexpr (MAXN >= 64) { col_pass<H, 64, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); } break;
+    case 32: col_pass<H, 32, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
+    default: col_pass<H, 64, INV, THREADS, OUT>(tf, P, buf, sOff, sAux, out, nb, stride); break;
   }
 }
 
@@ -378,12 +376,8 @@ __device__ __forceinline__ void multi_after_rows(const TfDev& th, const TfDev& t
 }
 
 // Shared memory limits residency to kSmemCtasPerSm CTAs per SM; the register budget
-// follows from that, so spills are never traded for occupancy that smem forbids.  The
-// short-line instance (MAXN <= 16) runs more threads per CTA on the same tile buffers:
-// its lines need far fewer registers, so the SM holds more warps.
+// follows from that, so spills are never traded for occupancy that smem forbids.
 constexpr int kSmemCtasPerSm = (227 * 1024) / (kSmemBytes + 3072);
-template <int THREADS, int MAXN>
-constexpr int kMinCtas = MAXN <= 16 ? kSmemCtasPerSm : kSmemCtasPerSm * 64 / THREADS;
 
 // Copies a small record (a multiple of 16 bytes) from global to shared memory
 // asynchronously, spread over the CTA's threads.
@@ -393,15 +387,14 @@ __device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes
     cp_async16(static_cast<unsigned char*>(dst) + i, static_cast<const unsigned char*>(src) + i);
 }
 
-template <bool INV, int THREADS, int MODE = kModePacked, int MAXN = 64>
-__global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kernel(FusedArgs a) {
+template <bool INV, int THREADS, int MODE = kModePacked>
+__global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_kernel(FusedArgs a) {
   constexpr bool MULTI = MODE == kModeMulti;
   constexpr bool FRAME_IN = !INV && MODE == kModeFrame;   // forward reading blocks from a frame
   constexpr int OUT = !INV || MODE < kModeFrame ? 0 : (MODE == kModeFrame ? 1 : 2);
   constexpr bool AUX = MODE == kModeMulti || MODE == kModeFrame || MODE == kModeFrameI16;
   constexpr bool F32_IN = INV || MODE == kModePackedF32;  // staged input is FP32 (else int16)
   static_assert(!(INV && MULTI), "the Multiple form is forward only");
-  static_assert(MAXN == 64 || MODE == kModePacked, "short-line instances are for packed blocks");
   static_assert(!(INV && MODE == kModePackedF32), "FP32 input is the inverse's own");
   static_assert(INV || MODE != kModeFrameI16, "int16 output is for the inverse");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -452,7 +445,7 @@ __global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kern
     if constexpr (FRAME_IN) {
       stage_frame<THREADS>(d0, sAux[0] + (d0.blk_begin & 3), a.in, a.frame_stride, reinterpret_cast<float*>(smem));
     } else {
-      stage_tile<F32_IN, THREADS, MAXN>(d0, sOff[0] + (d0.blk_begin & 3), a.in, reinterpret_cast<float*>(smem));
+      stage_tile<F32_IN, THREADS>(d0, sOff[0] + (d0.blk_begin & 3), a.in, reinterpret_cast<float*>(smem));
     }
     if (tn >= 0) {
       const TileDev d1 = a.tiles[tn];
@@ -483,7 +476,7 @@ __global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kern
       if constexpr (FRAME_IN) {
         stage_frame<THREADS>(dn, sAux[(k + 1) % 3] + (dn.blk_begin & 3), a.in, a.frame_stride, nbuf);
       } else {
-        stage_tile<F32_IN, THREADS, MAXN>(dn, sOff[(k + 1) % 3] + (dn.blk_begin & 3), a.in, nbuf);
+        stage_tile<F32_IN, THREADS>(dn, sOff[(k + 1) % 3] + (dn.blk_begin & 3), a.in, nbuf);
       }
       copy_async<THREADS>(&sTf[cur ^ 1][0], a.tfs + dn.tf_h, sizeof(TfDev));
       copy_async<THREADS>(&sTf[cur ^ 1][1], a.tfs + dn.tf_v, sizeof(TfDev));
@@ -513,8 +506,8 @@ __global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kern
         case 4: row_pass<4, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
         case 8: row_pass<8, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
         case 16: row_pass<16, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
-        case 32: if constexpr (MAXN >= 32) { row_pass<32, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); } break;
-        default: if constexpr (MAXN >= 64) { row_pass<64, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); } break;
+        case 32: row_pass<32, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
+        default: row_pass<64, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
       }
     }
     // (4)
@@ -537,15 +530,11 @@ __global__ void __launch_bounds__(THREADS, (kMinCtas<THREADS, MAXN>)) fused_kern
       const uint32_t* aux = sAux[AUX ? k % 3 : 0] + (td.blk_begin & 3);
       const int st = (int)a.frame_stride;
       switch (h) {
-        case 4: col_dispatch<4, INV, THREADS, OUT, MAXN>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
-        case 8: col_dispatch<8, INV, THREADS, OUT, MAXN>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
-        case 16: col_dispatch<16, INV, THREADS, OUT, MAXN>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
-        case 32:
-          if constexpr (MAXN >= 32) { col_dispatch<32, INV, THREADS, OUT, MAXN>(tf, a.params, buf, offs, aux, a.out, nb, w, st); }
-          break;
-        default:
-          if constexpr (MAXN >= 64) { col_dispatch<64, INV, THREADS, OUT, MAXN>(tf, a.params, buf, offs, aux, a.out, nb, w, st); }
-          break;
+        case 4: col_dispatch<4, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+        case 8: col_dispatch<8, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+        case 16: col_dispatch<16, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+        case 32: col_dispatch<32, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+        default: col_dispatch<64, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
       }
     }
     t = tn;
