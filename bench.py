@@ -402,6 +402,8 @@ def bench_config5(args, rank, dev, stream, flush, peak):
                 "fwd_ms": round(tf, 4), "inv_ms": round(ti, 4),
                 "fwd_frac": round(bf / (tf * 1e-3) / 1e9 / peak, 4), "inv_frac": round(bi / (ti * 1e-3) / 1e9 / peak, 4),
                 "flops_per_coef": round(fl / coefs, 2), "alu_fwd": alu_roofline(fl, tf), "alu_inv": alu_roofline(fl, ti),
+                "algorithmic_bytes": {"fwd": bf, "inv": bi},
+                "traffic": {"fwd": profiled_traffic("config5_fwd"), "inv": profiled_traffic("config5_inv")},
                 "roundtrip_max_abs_err": rt})
     # the exact transforms the adjustments stand in for, as dense products (Eq. 3)
     dense = [targets.dense_tf(targets.dst7(64)), targets.dense_tf(targets.dct8(64)), targets.dense_tf(targets.dct8(32))]
