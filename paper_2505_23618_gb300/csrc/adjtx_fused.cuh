@@ -32,15 +32,30 @@ __device__ __forceinline__ void stage_tile_w(const TileDev& td, const uint32_t* 
   constexpr int SH = sw_shift(W), MK = sw_mask(W);
   const int h = td.h, nb = td.nblk, lgh = lg2(h);
   if constexpr (F32) {
-    // FP32 chunks of 4 samples: W/4 per row
-    constexpr int LG_CPR = ilog2(W / 4);
-    const int lg_cpb = LG_CPR + lgh, total = nb << lg_cpb;
+    // FP32 chunks of 4 samples, W/4 per row, chunk q of row r at slot q ^ f(r).  THREADS is a
+    // multiple of the chunks per row, so a thread's chunk column q is fixed; blocks of at least
+    // THREADS chunks are walked block by block (one offset load per block), smaller ones with
+    // a fixed chunk per thread and a block stride.  (For the int16 forward the plain loop
+    // below measured faster.)
+    constexpr int LG_CPR = ilog2(W / 4), LG_T = ilog2(THREADS);
+    static_assert((THREADS & ((1 << LG_CPR) - 1)) == 0, "THREADS must be a multiple of the chunks per row");
     const float* src = static_cast<const float*>(in);
-    for (int g = threadIdx.x; g < total; g += THREADS) {
-      const int b = g >> lg_cpb, gg = g & ((1 << lg_cpb) - 1);
-      const int r = gg >> LG_CPR, q = gg & ((1 << LG_CPR) - 1);
-      const size_t off = (size_t)sOff[b] * 16;
-      cp_async16(buf + (b << (lgh + ilog2(W))) + r * W + ((q ^ ((r >> SH) & MK)) << 2), src + off + gg * 4);
+    const int lg_cpb = LG_CPR + lgh;
+    const int q = threadIdx.x & ((1 << LG_CPR) - 1);
+    if (lg_cpb >= LG_T) {
+      for (int b = 0; b < nb; ++b) {
+        float* bb = buf + (b << (lgh + ilog2(W)));
+        const float* sb = src + (size_t)sOff[b] * 16;
+        for (int c = threadIdx.x; c < (1 << lg_cpb); c += THREADS) {
+          const int r = c >> LG_CPR;
+          cp_async16(bb + r * W + ((q ^ ((r >> SH) & MK)) << 2), sb + c * 4);
+        }
+      }
+    } else {
+      const int c = threadIdx.x & ((1 << lg_cpb) - 1), r = c >> LG_CPR;
+      const int doff = r * W + ((q ^ ((r >> SH) & MK)) << 2);
+      for (int b = threadIdx.x >> lg_cpb; b < nb; b += THREADS >> lg_cpb)
+        cp_async16(buf + (b << (lgh + ilog2(W))) + doff, src + (size_t)sOff[b] * 16 + c * 4);
     }
   } else if constexpr (W >= 8) {
     // int16 chunks of 8 samples: W/8 per row, placed at FP32 chunk slot q ^ f(r)
