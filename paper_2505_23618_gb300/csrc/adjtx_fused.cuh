@@ -33,16 +33,16 @@ __device__ __forceinline__ void stage_tile_w(const TileDev& td, const uint32_t* 
   const int h = td.h, nb = td.nblk, lgh = lg2(h);
   if constexpr (F32) {
     // FP32 chunks of 4 samples, W/4 per row, chunk q of row r at slot q ^ f(r).  THREADS is a
-    // multiple of the chunks per row, so a thread's chunk column q is fixed; blocks of at least
-    // THREADS chunks are walked block by block (one offset load per block), smaller ones with
-    // a fixed chunk per thread and a block stride.  (For the int16 forward the plain loop
-    // below measured faster.)
+    // multiple of the chunks per row, so a thread's chunk column q is fixed; blocks of more than
+    // THREADS chunks are walked block by block (one offset load per block), smaller ones with a
+    // fixed chunk per thread and a block stride.  (For the int16 forward the plain loop below
+    // measured faster.)
     constexpr int LG_CPR = ilog2(W / 4), LG_T = ilog2(THREADS);
     static_assert((THREADS & ((1 << LG_CPR) - 1)) == 0, "THREADS must be a multiple of the chunks per row");
     const float* src = static_cast<const float*>(in);
     const int lg_cpb = LG_CPR + lgh;
     const int q = threadIdx.x & ((1 << LG_CPR) - 1);
-    if (lg_cpb >= LG_T) {
+    if (lg_cpb > LG_T) {
       for (int b = 0; b < nb; ++b) {
         float* bb = buf + (b << (lgh + ilog2(W)));
         const float* sb = src + (size_t)sOff[b] * 16;
