@@ -8,13 +8,26 @@ def _torch():
     return torch
 
 
+def _check(t, dtypes, plan, what):
+    """A contiguous CUDA tensor of one of `dtypes` holding at least plan.total samples (the
+    kernels read and write plan.total samples; a shorter buffer would be overrun)."""
+    torch = _torch()
+    if t.dtype not in dtypes or not t.is_cuda:
+        names = " or ".join(str(d).replace("torch.", "") for d in dtypes)
+        raise TypeError(f"{what} must be a CUDA {names} tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() < plan.total:
+        raise ValueError(f"{what} holds {t.numel()} samples, the plan's blocks need {plan.total}")
+
+
 def forward(plan, resid, out=None, stream=None):
     """int16 residuals (CUDA tensor, plan.total samples) -> FP32 coefficients."""
     torch = _torch()
-    if resid.dtype != torch.int16 or not resid.is_cuda:
-        raise TypeError("resid must be a CUDA int16 tensor")
+    _check(resid, (torch.int16,), plan, "resid")
     if out is None:
         out = torch.zeros(plan.total, dtype=torch.float32, device=resid.device)
+    _check(out, (torch.float32,), plan, "out")
     s = stream if stream is not None else torch.cuda.current_stream(resid.device)
     plan.fwd(resid, out, s)
     return out
@@ -23,10 +36,10 @@ def forward(plan, resid, out=None, stream=None):
 def inverse(plan, coef, out=None, stream=None):
     """FP32 coefficients (CUDA tensor) -> FP32 reconstruction."""
     torch = _torch()
-    if coef.dtype != torch.float32 or not coef.is_cuda:
-        raise TypeError("coef must be a CUDA float32 tensor")
+    _check(coef, (torch.float32,), plan, "coef")
     if out is None:
         out = torch.zeros(plan.total, dtype=torch.float32, device=coef.device)
+    _check(out, (torch.float32,), plan, "out")
     s = stream if stream is not None else torch.cuda.current_stream(coef.device)
     plan.inv(coef, out, s)
     return out
@@ -42,8 +55,7 @@ def forward_multiple(plan, resid, side_offsets=None, stream=None):
     regions of the four DST-7 / DCT-8 pairings, side offsets).  Prepares the plan's block
     list for this form unless ``side_offsets`` from an earlier preparation is given."""
     torch = _torch()
-    if resid.dtype != torch.int16 or not resid.is_cuda:
-        raise TypeError("resid must be a CUDA int16 tensor")
+    _check(resid, (torch.int16,), plan, "resid")
     if side_offsets is None:
         side_offsets = plan.prepare_multiple()
     y = torch.zeros(plan.total, dtype=torch.float32, device=resid.device)
@@ -121,6 +133,9 @@ def _make_autograd():
 
         @staticmethod
         def forward(ctx, x, params, plan):
+            _check(x, (torch.int16, torch.float32), plan, "x")
+            if params.dim() != 1 or params.numel() != _layout(plan)[-1]:
+                raise ValueError(f"params must be a vector of {_layout(plan)[-1]} entries (param_vector layout)")
             vals = params.detach().to("cpu", torch.float64).numpy()
             cur = getattr(plan, "_param_values", None)
             if cur is None or cur.shape != vals.shape or not np.array_equal(cur, vals):
@@ -129,10 +144,8 @@ def _make_autograd():
             s = torch.cuda.current_stream(x.device)
             if x.dtype == torch.int16:
                 plan.fwd(x, y, s)
-            elif x.dtype == torch.float32:
-                plan.fwd_f32(x.contiguous(), y, s)
             else:
-                raise TypeError("x must be a CUDA int16 or float32 tensor")
+                plan.fwd_f32(x, y, s)
             ctx.plan, ctx.vals, ctx.p_dtype = plan, vals, params.dtype
             ctx.save_for_backward(x)
             return y

@@ -160,3 +160,30 @@ def test_cayley_chain_through_torch_matches_oracle():
     _, rgp = oracle_grads(wl_o, G)
     ref = O.cayley_grad(w0, K, rgp[0].reshape(K, K), D)
     assert np.linalg.norm(gw - ref) / np.linalg.norm(ref) <= REL
+
+
+def test_torch_api_rejects_short_or_wrong_buffers():
+    """Buffers shorter than the plan's samples, non-contiguous ones and a parameter vector of the
+    wrong length are refused on the host, before any launch."""
+    import torch
+    import paper_2505_23618_gb300 as adj
+    wl = synth.random_small(17, 20)
+    with adj.Plan(wl.tfs) as plan:
+        plan.set_blocks(wl.blocks, wl.total)
+        x = torch.from_numpy(wl.data).cuda()
+        with pytest.raises(ValueError):
+            adj.forward(plan, x[: wl.total - 16])
+        with pytest.raises(ValueError):
+            adj.inverse(plan, torch.zeros(wl.total - 16, device="cuda"))
+        with pytest.raises(ValueError):
+            adj.forward(plan, x, out=torch.zeros(wl.total - 4, device="cuda"))
+        with pytest.raises(ValueError):
+            adj.forward(plan, torch.zeros((2, wl.total), dtype=torch.int16, device="cuda")[:, 0])
+        with pytest.raises(TypeError):
+            adj.forward(plan, x.float())
+        p = adj.param_vector(plan, device="cuda")
+        with pytest.raises(ValueError):
+            adj.adjusted_transform(x, p[:-1], plan)
+        y = adj.adjusted_transform(x, p, plan)     # the right sizes still work
+        torch.cuda.synchronize()
+        assert y.numel() == wl.total
