@@ -118,7 +118,9 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
  * Give the plan its block list (host memory, n_blocks records) for buffers of
  * total_coefs samples.  Validates sizes, transform indices, alignment, bounds and
  * non-overlap; groups blocks of equal (w, h, tf_h, tf_v) into shared-memory tiles in
- * storage order and uploads the tile list.  May be called again to replace the list.
+ * storage order, sorts the tiles by the code they run and cuts them into one scheduling
+ * range per SM of about equal estimated run time (most expensive tiles first in each),
+ * and uploads the tile list.  May be called again to replace the list.
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, PARAM_MISMATCH, MISALIGNED, CUDA.
  */
 int adj_plan_set_blocks(adj_plan_t* plan, const adj_block_t* blocks, int64_t n_blocks,
