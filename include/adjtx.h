@@ -127,6 +127,29 @@ int adj_plan_set_blocks(adj_plan_t* plan, const adj_block_t* blocks, int64_t n_b
                         int64_t total_coefs);
 
 /*
+ * The scheduling layout adj_plan_set_blocks builds, computed on the host alone (no device is
+ * used): the transforms and blocks are validated as by adj_plan_create and
+ * adj_plan_set_blocks, then grouped into tiles and cut into ranges for a GPU of n_sm SMs
+ * under the default tuning.  Outputs (each optional; the counts are always written):
+ *   tiles[t]    tile t in launch order: its first entry in `list`, block count, w, h, tf_h, tf_v;
+ *   costs[t]    its estimated run time (microseconds, the planner's model);
+ *   list        block offsets / 16 of every tile, each tile's run 4-entry aligned, 4 spare
+ *               entries at the end (*list_len entries);
+ *   range_begin first tile of each range, *n_ranges + 1 entries (the last one = *n_tiles).
+ * tiles and costs hold tiles_cap records, list list_cap entries, range_begin ranges_cap + 1.
+ * Errors: as those two calls; INVALID_ARG also when an output array is too small (the counts
+ * are still written) or n_sm is outside 1..256.
+ */
+typedef struct {
+  uint32_t list_begin;            /* first entry of the tile's block list */
+  uint16_t nblk, w, h, tf_h, tf_v, pad;
+} adj_tile_info_t;
+int adj_layout_preview(const adj_1d_desc_t* tfs, int32_t n_tfs, const adj_block_t* blocks, int64_t n_blocks,
+                       int64_t total_coefs, int32_t n_sm, adj_tile_info_t* tiles, double* costs,
+                       int64_t tiles_cap, int64_t* n_tiles, uint32_t* list, int64_t list_cap, int64_t* list_len,
+                       uint32_t* range_begin, int32_t ranges_cap, int32_t* n_ranges);
+
+/*
  * Replace the parameter values (angles, Q) of all transforms without changing their
  * structure (n, core, kind, layer parities, K).  Asynchronous on the legacy stream
  * ordering of cudaMemcpy: completes before it returns.

@@ -6,13 +6,14 @@ post-adjustment (H = C B A, Eq. 1).  All arithmetic runs in the hand-written CUD
 library behind the C ABI of include/adjtx.h; this package only marshals arguments.
 """
 
-from ._lib import (ADJ_OK, BLOCK_DTYPE, ERR_CODE, ERRORS, EXPORTED, LIB_PATH, AdjError,  # noqa: F401
-                   Plan, check, lib, load)
+from ._lib import (ADJ_OK, BLOCK_DTYPE, ERR_CODE, ERRORS, EXPORTED, LIB_PATH, TILE_INFO_DTYPE,  # noqa: F401
+                   AdjError, Plan, check, layout_preview, lib, load)
 from .torch_api import (adjusted_transform, autograd_function, forward, forward_multiple, inverse,  # noqa: F401
                         param_vector, roundtrip)
 
 __all__ = ["Plan", "AdjError", "forward", "forward_multiple", "inverse", "roundtrip", "adjusted_transform",
-           "autograd_function", "param_vector", "AdjFn", "BLOCK_DTYPE", "lib", "LIB_PATH", "EXPORTED"]
+           "autograd_function", "param_vector", "AdjFn", "BLOCK_DTYPE", "TILE_INFO_DTYPE", "layout_preview", "lib",
+           "LIB_PATH", "EXPORTED"]
 
 
 def __getattr__(name):

@@ -34,7 +34,7 @@ EXPORTED = (
     "adj_plan_param_layout", "adj_coding_gain_proxy", "adj_plan_get_tuning", "adj_plan_set_tuning",
     "adj_plan_autotune", "adj_plan_prepare_multiple", "adj_transform_fwd_multiple",
     "adj_plan_set_frame_blocks", "adj_transform_fwd_frame", "adj_transform_inv_frame",
-    "adj_transform_fwd_f32",
+    "adj_transform_fwd_f32", "adj_layout_preview",
 )
 DTYPE_INT16, DTYPE_FP32 = 0, 1
 GRAPH_FWD, GRAPH_INV, GRAPH_FWD_PLAIN, GRAPH_INV_PLAIN, GRAPH_ROUNDTRIP, GRAPH_FWD_MULTIPLE = range(6)
@@ -94,6 +94,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.adj_plan_set_frame_blocks.argtypes = [vp, vp, i64, i32, i32, i32]
     lib.adj_transform_fwd_frame.argtypes = [vp, vp, vp, vp]
     lib.adj_transform_inv_frame.argtypes = [vp, vp, vp, vp, vp]
+    lib.adj_layout_preview.argtypes = [C.POINTER(Adj1dDesc), i32, vp, i64, i64, i32, vp, vp, i64,
+                                       C.POINTER(C.c_int64), vp, i64, C.POINTER(C.c_int64), vp, i32,
+                                       C.POINTER(C.c_int32)]
     lib.adj_graph_create.argtypes = [vp, i32, vp, vp, vp, C.POINTER(vp)]
     lib.adj_graph_launch.argtypes = [vp, vp]
     lib.adj_graph_destroy.argtypes = [vp]
@@ -334,3 +337,27 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+TILE_INFO_DTYPE = np.dtype([("list_begin", "<u4"), ("nblk", "<u2"), ("w", "<u2"), ("h", "<u2"),
+                            ("tf_h", "<u2"), ("tf_v", "<u2"), ("pad", "<u2")])
+
+
+def layout_preview(tfs, blocks: np.ndarray, total: int, n_sm: int = 152) -> dict:
+    """The tile and range layout adj_plan_set_blocks would build for a GPU of n_sm SMs, computed
+    on the host (adj_layout_preview; no device needed): tiles (TILE_INFO_DTYPE) in launch order,
+    their estimated costs, the block-offset list and the range starts."""
+    L = lib()
+    d = _DescArray(list(tfs))
+    b = np.ascontiguousarray(blocks, dtype=BLOCK_DTYPE)
+    nt, nl, nr = C.c_int64(0), C.c_int64(0), C.c_int32(0)
+    args = (d.arr, d.n, _ptr(b) if b.size else None, int(b.size), int(total), int(n_sm))
+    check(L.adj_layout_preview(*args, None, None, 0, C.byref(nt), None, 0, C.byref(nl), None, 0, C.byref(nr)))
+    tiles = np.zeros(nt.value, dtype=TILE_INFO_DTYPE)
+    costs = np.zeros(nt.value, dtype=np.float64)
+    lst = np.zeros(max(1, nl.value), dtype=np.uint32)
+    rbeg = np.zeros(nr.value + 1, dtype=np.uint32)
+    check(L.adj_layout_preview(*args, _ptr(tiles) if tiles.size else None, _ptr(costs) if costs.size else None,
+                               int(nt.value), C.byref(nt), _ptr(lst), int(lst.size), C.byref(nl), _ptr(rbeg),
+                               int(nr.value), C.byref(nr)))
+    return {"tiles": tiles, "costs": costs, "list": lst[:nl.value], "range_begin": rbeg}

@@ -753,6 +753,36 @@ int run_host(adj_plan* p, bool inverse, const void* h_in, float* h_out, cudaStre
 
 }  // namespace
 
+// Validates a block list against the plan's transforms (sizes, transform indices, alignment,
+// bounds, no overlap) and stores it sorted by offset (p->blocks, p->orig).  Host only.
+static int accept_blocks(adj_plan* p, const adj_block_t* blocks, int64_t n_blocks, int64_t total_coefs) {
+  if (n_blocks < 0 || (n_blocks > 0 && !blocks)) return fail(ADJ_ERR_INVALID_ARG, "bad block list");
+  if (total_coefs < 0 || total_coefs > (int64_t(1) << 36)) return fail(ADJ_ERR_INVALID_ARG, "total_coefs %lld out of range", (long long)total_coefs);
+  const int n_tfs = (int)p->tfs.size();
+  for (int64_t i = 0; i < n_blocks; ++i) {
+    const adj_block_t& b = blocks[i];
+    if (!is_size(b.w) || !is_size(b.h)) return fail(ADJ_ERR_UNSUPPORTED_SIZE, "block %lld: %dx%d", (long long)i, b.w, b.h);
+    if (b.tf_h >= n_tfs || b.tf_v >= n_tfs) return fail(ADJ_ERR_INVALID_ARG, "block %lld: transform index out of range", (long long)i);
+    if (p->tfs[b.tf_h].n != b.w || p->tfs[b.tf_v].n != b.h)
+      return fail(ADJ_ERR_PARAM_MISMATCH, "block %lld: %dx%d with transforms of length %d (h) and %d (v)",
+                  (long long)i, b.w, b.h, p->tfs[b.tf_h].n, p->tfs[b.tf_v].n);
+    if (b.offset < 0 || b.offset % 16) return fail(ADJ_ERR_MISALIGNED, "block %lld: offset %lld", (long long)i, (long long)b.offset);
+    if (b.offset + (int64_t)b.w * b.h > total_coefs) return fail(ADJ_ERR_INVALID_ARG, "block %lld extends past total_coefs", (long long)i);
+  }
+  std::vector<int64_t> order(n_blocks);
+  for (int64_t i = 0; i < n_blocks; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return blocks[a].offset < blocks[b].offset; });
+  for (int64_t i = 1; i < n_blocks; ++i) {
+    const adj_block_t &a = blocks[order[i - 1]], &b = blocks[order[i]];
+    if (a.offset + (int64_t)a.w * a.h > b.offset) return fail(ADJ_ERR_INVALID_ARG, "blocks %lld and %lld overlap", (long long)order[i - 1], (long long)order[i]);
+  }
+  p->blocks.clear();
+  p->blocks.reserve(n_blocks);
+  for (int64_t i : order) p->blocks.push_back(blocks[i]);
+  p->orig = order;
+  return ADJ_OK;
+}
+
 extern "C" {
 
 const char* adj_last_error(void) { return g_err.c_str(); }
@@ -944,40 +974,54 @@ int adj_plan_update_params(adj_plan_t* p, const adj_1d_desc_t* tfs, int32_t n_tf
 int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_blocks, int64_t total_coefs) {
   g_err.clear();
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
-  if (n_blocks < 0 || (n_blocks > 0 && !blocks)) return fail(ADJ_ERR_INVALID_ARG, "bad block list");
-  if (total_coefs < 0 || total_coefs > (int64_t(1) << 36)) return fail(ADJ_ERR_INVALID_ARG, "total_coefs %lld out of range", (long long)total_coefs);
-  const int n_tfs = (int)p->tfs.size();
-  for (int64_t i = 0; i < n_blocks; ++i) {
-    const adj_block_t& b = blocks[i];
-    if (!is_size(b.w) || !is_size(b.h)) return fail(ADJ_ERR_UNSUPPORTED_SIZE, "block %lld: %dx%d", (long long)i, b.w, b.h);
-    if (b.tf_h >= n_tfs || b.tf_v >= n_tfs) return fail(ADJ_ERR_INVALID_ARG, "block %lld: transform index out of range", (long long)i);
-    if (p->tfs[b.tf_h].n != b.w || p->tfs[b.tf_v].n != b.h)
-      return fail(ADJ_ERR_PARAM_MISMATCH, "block %lld: %dx%d with transforms of length %d (h) and %d (v)",
-                  (long long)i, b.w, b.h, p->tfs[b.tf_h].n, p->tfs[b.tf_v].n);
-    if (b.offset < 0 || b.offset % 16) return fail(ADJ_ERR_MISALIGNED, "block %lld: offset %lld", (long long)i, (long long)b.offset);
-    if (b.offset + (int64_t)b.w * b.h > total_coefs) return fail(ADJ_ERR_INVALID_ARG, "block %lld extends past total_coefs", (long long)i);
-  }
-  std::vector<int64_t> order(n_blocks);
-  for (int64_t i = 0; i < n_blocks; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return blocks[a].offset < blocks[b].offset; });
-  for (int64_t i = 1; i < n_blocks; ++i) {
-    const adj_block_t &a = blocks[order[i - 1]], &b = blocks[order[i]];
-    if (a.offset + (int64_t)a.w * a.h > b.offset) return fail(ADJ_ERR_INVALID_ARG, "blocks %lld and %lld overlap", (long long)order[i - 1], (long long)order[i]);
-  }
-
-  p->blocks.clear();
-  p->blocks.reserve(n_blocks);
-  for (int64_t i : order) p->blocks.push_back(blocks[i]);
-  p->orig = order;
+  int rc = accept_blocks(p, blocks, n_blocks, total_coefs);
+  if (rc) return rc;
   p->multi = false;
   p->side_off.clear();
   p->frame = false;
   p->frame_off.clear();
   p->n_blocks = n_blocks;
   p->total = total_coefs;
-  const int rc = build_layout(p);
+  rc = build_layout(p);
   if (rc) return rc;
   p->has_blocks = true;
+  return ADJ_OK;
+}
+
+int adj_layout_preview(const adj_1d_desc_t* tfs, int32_t n_tfs, const adj_block_t* blocks, int64_t n_blocks,
+                       int64_t total_coefs, int32_t n_sm, adj_tile_info_t* tiles, double* costs, int64_t tiles_cap,
+                       int64_t* n_tiles, uint32_t* list, int64_t list_cap, int64_t* list_len, uint32_t* range_begin,
+                       int32_t ranges_cap, int32_t* n_ranges) {
+  g_err.clear();
+  if (!tfs || n_tfs <= 0 || n_tfs > 65535) return fail(ADJ_ERR_INVALID_ARG, "bad transform table");
+  if (n_sm < 1 || n_sm > kMaxRanges) return fail(ADJ_ERR_INVALID_ARG, "n_sm %d out of range", n_sm);
+  if (!n_tiles || !list_len || !n_ranges) return fail(ADJ_ERR_INVALID_ARG, "null count pointer");
+  adj_plan pl;
+  pl.tfs.resize(n_tfs);
+  int rc;
+  for (int i = 0; i < n_tfs; ++i)
+    if ((rc = validate_tf(tfs[i], i, &pl.tfs[i]))) return rc;
+  if ((rc = accept_blocks(&pl, blocks, n_blocks, total_coefs))) return rc;
+  for (int i = 0; i < 25; ++i) pl.tuning.cap_div[i] = 1;
+  pl.tuning.ctas_per_sm = 0;
+  pl.tuning.ranges_per_sm = 1;
+  pl.n_sm = n_sm;
+  TileSet ts;
+  build_tiles(&pl, 0, pl.blocks.size(), &ts);
+  *n_tiles = (int64_t)ts.tiles.size();
+  *list_len = (int64_t)ts.tblk.size();
+  *n_ranges = ts.n_ranges;
+  if ((tiles || costs) && tiles_cap < *n_tiles) return fail(ADJ_ERR_INVALID_ARG, "tile arrays hold %lld, need %lld", (long long)tiles_cap, (long long)*n_tiles);
+  if (list && list_cap < *list_len) return fail(ADJ_ERR_INVALID_ARG, "list holds %lld, needs %lld", (long long)list_cap, (long long)*list_len);
+  if (range_begin && ranges_cap < ts.n_ranges) return fail(ADJ_ERR_INVALID_ARG, "range array holds %d + 1, needs %d + 1", ranges_cap, ts.n_ranges);
+  static_assert(sizeof(adj_tile_info_t) == sizeof(TileDev), "tile record layout");
+  for (size_t t = 0; t < ts.tiles.size(); ++t) {
+    const TileDev& d = ts.tiles[t];
+    if (tiles) tiles[t] = adj_tile_info_t{d.blk_begin, d.nblk, d.w, d.h, d.tf_h, d.tf_v, 0};
+    if (costs) costs[t] = tile_cost(&pl, d);
+  }
+  if (list && !ts.tblk.empty()) std::memcpy(list, ts.tblk.data(), ts.tblk.size() * sizeof(uint32_t));
+  if (range_begin && !ts.rbeg.empty()) std::memcpy(range_begin, ts.rbeg.data(), ts.rbeg.size() * sizeof(uint32_t));
   return ADJ_OK;
 }
 
