@@ -26,7 +26,9 @@
  * Conventions
  *   - All calls return ADJ_OK (0) or a negative ADJ_ERR_* code; nothing aborts or
  *     throws across this boundary.  adj_last_error() returns a message for the last
- *     failing call of the calling thread.
+ *     failing call of the calling thread.  Calls that build host-side tables (plan
+ *     creation and updates, block lists, tuning, graphs, the *_host entry points and
+ *     adj_layout_preview) also return ADJ_ERR_NO_MEMORY when host memory runs out.
  *   - "stream" arguments are cudaStream_t values passed as void* (NULL = legacy
  *     default stream).  Device entry points are asynchronous with respect to the host:
  *     a kernel fault surfaces at the caller's next synchronisation.
@@ -54,7 +56,9 @@ enum {
                                     update_params that changes structure */
   ADJ_ERR_MISALIGNED = -4,       /* block offset not a multiple of 16 samples; buffer not 16-B aligned */
   ADJ_ERR_CUDA = -5,             /* a CUDA runtime call failed (message in adj_last_error) */
-  ADJ_ERR_NO_BLOCKS = -6         /* transform called before adj_plan_set_blocks */
+  ADJ_ERR_NO_BLOCKS = -6,        /* transform called before adj_plan_set_blocks */
+  ADJ_ERR_NO_MEMORY = -7         /* host memory allocation failed; a plan the call was changing
+                                    keeps its parameters but loses its block list */
 };
 
 /* Core B (Section 2.1). */

@@ -22,6 +22,7 @@ ERRORS = {
     -4: "ADJ_ERR_MISALIGNED",
     -5: "ADJ_ERR_CUDA",
     -6: "ADJ_ERR_NO_BLOCKS",
+    -7: "ADJ_ERR_NO_MEMORY",
 }
 ERR_CODE = {v: k for k, v in ERRORS.items()}
 

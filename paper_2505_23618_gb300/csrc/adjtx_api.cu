@@ -7,6 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <exception>
+#include <memory>
+#include <new>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -18,16 +21,33 @@ using namespace adjtx;
 
 namespace {
 
-thread_local std::string g_err;
+// Message of the calling thread's last failed call.  A fixed buffer: reporting an error
+// never allocates.
+thread_local char g_err[512];
+
+void clear_error() { g_err[0] = '\0'; }
 
 int fail(int code, const char* fmt, ...) {
-  char buf[512];
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
   va_end(ap);
-  g_err = buf;
   return code;
+}
+
+// Maps the C++ exception in flight (a failed host allocation, in practice) to an error code.
+// Called from the catch-all handler of every entry point that allocates host memory, so that
+// no exception crosses the C ABI.
+int entry_exception() {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return fail(ADJ_ERR_NO_MEMORY, "host memory allocation failed");
+  } catch (const std::exception& e) {
+    return fail(ADJ_ERR_NO_MEMORY, "host allocation: %s", e.what());
+  } catch (...) {
+    return fail(ADJ_ERR_NO_MEMORY, "unknown C++ exception");
+  }
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -229,10 +249,11 @@ void materialise(const std::vector<TfHost>& tfs, std::vector<float>* params, std
   if (params->empty()) params->resize(4, 0.f);
 }
 
-int upload_params(adj_plan* p) {
+// Uploads the tables of `tfs` (the plan's transforms, or their replacement).
+int upload_params(adj_plan* p, const std::vector<TfHost>& tfs) {
   std::vector<float> params;
   std::vector<TfDev> devs;
-  materialise(p->tfs, &params, &devs);
+  materialise(tfs, &params, &devs);
   if (!p->d_params) {
     CUDA_TRY(cudaMalloc(&p->d_params, params.size() * sizeof(float)));
     CUDA_TRY(cudaMalloc(&p->d_tfs, std::max<size_t>(1, devs.size()) * sizeof(TfDev)));
@@ -758,6 +779,10 @@ int run_host(adj_plan* p, bool inverse, const void* h_in, float* h_out, cudaStre
 static int accept_blocks(adj_plan* p, const adj_block_t* blocks, int64_t n_blocks, int64_t total_coefs) {
   if (n_blocks < 0 || (n_blocks > 0 && !blocks)) return fail(ADJ_ERR_INVALID_ARG, "bad block list");
   if (total_coefs < 0 || total_coefs > (int64_t(1) << 36)) return fail(ADJ_ERR_INVALID_ARG, "total_coefs %lld out of range", (long long)total_coefs);
+  // disjoint blocks of at least 16 samples: no more than total_coefs / 16 of them (which also
+  // keeps every block index within the 32-bit tile lists)
+  if (n_blocks > total_coefs / 16)
+    return fail(ADJ_ERR_INVALID_ARG, "%lld blocks cannot fit in %lld coefficients", (long long)n_blocks, (long long)total_coefs);
   const int n_tfs = (int)p->tfs.size();
   for (int64_t i = 0; i < n_blocks; ++i) {
     const adj_block_t& b = blocks[i];
@@ -767,7 +792,7 @@ static int accept_blocks(adj_plan* p, const adj_block_t* blocks, int64_t n_block
       return fail(ADJ_ERR_PARAM_MISMATCH, "block %lld: %dx%d with transforms of length %d (h) and %d (v)",
                   (long long)i, b.w, b.h, p->tfs[b.tf_h].n, p->tfs[b.tf_v].n);
     if (b.offset < 0 || b.offset % 16) return fail(ADJ_ERR_MISALIGNED, "block %lld: offset %lld", (long long)i, (long long)b.offset);
-    if (b.offset + (int64_t)b.w * b.h > total_coefs) return fail(ADJ_ERR_INVALID_ARG, "block %lld extends past total_coefs", (long long)i);
+    if (b.offset > total_coefs - (int64_t)b.w * b.h) return fail(ADJ_ERR_INVALID_ARG, "block %lld extends past total_coefs", (long long)i);
   }
   std::vector<int64_t> order(n_blocks);
   for (int64_t i = 0; i < n_blocks; ++i) order[i] = i;
@@ -785,15 +810,15 @@ static int accept_blocks(adj_plan* p, const adj_block_t* blocks, int64_t n_block
 
 extern "C" {
 
-const char* adj_last_error(void) { return g_err.c_str(); }
+const char* adj_last_error(void) { return g_err; }
 
 struct adj_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 
-int adj_graph_create(adj_plan_t* p, int32_t what, const void* d_in, float* d_out, float* d_out2, adj_graph_t** graph) {
-  g_err.clear();
+int adj_graph_create(adj_plan_t* p, int32_t what, const void* d_in, float* d_out, float* d_out2, adj_graph_t** graph) try {
+  clear_error();
   if (!graph) return fail(ADJ_ERR_INVALID_ARG, "null graph pointer");
   *graph = nullptr;
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
@@ -827,7 +852,11 @@ int adj_graph_create(adj_plan_t* p, int32_t what, const void* d_in, float* d_out
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  adj_graph* out = new adj_graph();
+  adj_graph* out = new (std::nothrow) adj_graph();
+  if (!out) {
+    cudaGraphDestroy(g);
+    return fail(ADJ_ERR_NO_MEMORY, "host memory allocation failed");
+  }
   out->graph = g;
   e = cudaGraphInstantiate(&out->exec, g, 0);
   if (e != cudaSuccess) {
@@ -837,10 +866,12 @@ int adj_graph_create(adj_plan_t* p, int32_t what, const void* d_in, float* d_out
   }
   *graph = out;
   return ADJ_OK;
+} catch (...) {
+  return entry_exception();
 }
 
 int adj_graph_launch(adj_graph_t* g, void* stream) {
-  g_err.clear();
+  clear_error();
   if (!g) return fail(ADJ_ERR_INVALID_ARG, "null graph");
   CUDA_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
   return ADJ_OK;
@@ -856,12 +887,12 @@ void adj_graph_destroy(adj_graph_t* g) {
 }  // extern "C"
 
 // Lets other translation units of the library report errors through adj_last_error().
-void adjtx::set_last_error(const char* msg) { g_err = msg; }
+void adjtx::set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 
 extern "C" {
 
-int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, int32_t flags) {
-  g_err.clear();
+int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, int32_t flags) try {
+  clear_error();
   if (!plan) return fail(ADJ_ERR_INVALID_ARG, "null plan pointer");
   *plan = nullptr;
   if (n_tfs < 0 || n_tfs > 65535 || (n_tfs > 0 && !tfs)) return fail(ADJ_ERR_INVALID_ARG, "bad transform table (n_tfs=%d)", n_tfs);
@@ -871,15 +902,14 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     int rc = validate_tf(tfs[i], i, &hs[i]);
     if (rc) return rc;
   }
-  adj_plan* p = new adj_plan();
+  // the plan is handed out only complete: an error or exception on the way frees it
+  std::unique_ptr<adj_plan, void (*)(adj_plan_t*)> owner(new adj_plan(), adj_plan_destroy);
+  adj_plan* p = owner.get();
   p->tfs = std::move(hs);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "device query");
-  }
-  int rc = upload_params(p);
+  if (e != cudaSuccess) return cuda_fail(e, "device query");
+  int rc = upload_params(p, p->tfs);
   // gradient layouts: accumulator side^2 per transform (band n, post / dense kt) and the
   // gradient entries (band: angles, post: K x K, dense: n x n)
   for (const TfHost& t : p->tfs) {
@@ -943,16 +973,15 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     p->tuning.ranges_per_sm = 1;
     apply_grid(p);
   }
-  if (rc) {
-    adj_plan_destroy(p);
-    return rc;
-  }
-  *plan = p;
+  if (rc) return rc;
+  *plan = owner.release();
   return ADJ_OK;
+} catch (...) {
+  return entry_exception();
 }
 
-int adj_plan_update_params(adj_plan_t* p, const adj_1d_desc_t* tfs, int32_t n_tfs) {
-  g_err.clear();
+int adj_plan_update_params(adj_plan_t* p, const adj_1d_desc_t* tfs, int32_t n_tfs) try {
+  clear_error();
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
   if (n_tfs != (int)p->tfs.size() || (n_tfs > 0 && !tfs))
     return fail(ADJ_ERR_PARAM_MISMATCH, "update with %d transforms, plan has %zu", n_tfs, p->tfs.size());
@@ -964,15 +993,15 @@ int adj_plan_update_params(adj_plan_t* p, const adj_1d_desc_t* tfs, int32_t n_tf
     if (a.n != b.n || a.core != b.core || a.kind != b.kind || a.n_layers != b.n_layers || a.parity != b.parity || a.k != b.k)
       return fail(ADJ_ERR_PARAM_MISMATCH, "tf %d: structure changed", i);
   }
-  std::vector<TfHost> old = std::move(p->tfs);
-  p->tfs = std::move(hs);
-  int rc = upload_params(p);
-  if (rc) p->tfs = std::move(old);
+  const int rc = upload_params(p, hs);
+  if (!rc) p->tfs.swap(hs);
   return rc;
+} catch (...) {
+  return entry_exception();
 }
 
-int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_blocks, int64_t total_coefs) {
-  g_err.clear();
+int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_blocks, int64_t total_coefs) try {
+  clear_error();
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
   int rc = accept_blocks(p, blocks, n_blocks, total_coefs);
   if (rc) return rc;
@@ -986,13 +1015,16 @@ int adj_plan_set_blocks(adj_plan_t* p, const adj_block_t* blocks, int64_t n_bloc
   if (rc) return rc;
   p->has_blocks = true;
   return ADJ_OK;
+} catch (...) {
+  if (p) free_blocks(p);
+  return entry_exception();
 }
 
 int adj_layout_preview(const adj_1d_desc_t* tfs, int32_t n_tfs, const adj_block_t* blocks, int64_t n_blocks,
                        int64_t total_coefs, int32_t n_sm, adj_tile_info_t* tiles, double* costs, int64_t tiles_cap,
                        int64_t* n_tiles, uint32_t* list, int64_t list_cap, int64_t* list_len, uint32_t* range_begin,
-                       int32_t ranges_cap, int32_t* n_ranges) {
-  g_err.clear();
+                       int32_t ranges_cap, int32_t* n_ranges) try {
+  clear_error();
   if (!tfs || n_tfs <= 0 || n_tfs > 65535) return fail(ADJ_ERR_INVALID_ARG, "bad transform table");
   if (n_sm < 1 || n_sm > kMaxRanges) return fail(ADJ_ERR_INVALID_ARG, "n_sm %d out of range", n_sm);
   if (!n_tiles || !list_len || !n_ranges) return fail(ADJ_ERR_INVALID_ARG, "null count pointer");
@@ -1023,26 +1055,28 @@ int adj_layout_preview(const adj_1d_desc_t* tfs, int32_t n_tfs, const adj_block_
   if (list && !ts.tblk.empty()) std::memcpy(list, ts.tblk.data(), ts.tblk.size() * sizeof(uint32_t));
   if (range_begin && !ts.rbeg.empty()) std::memcpy(range_begin, ts.rbeg.data(), ts.rbeg.size() * sizeof(uint32_t));
   return ADJ_OK;
+} catch (...) {
+  return entry_exception();
 }
 
 int adj_transform_fwd(adj_plan_t* p, const int16_t* d_resid, float* d_coef, void* stream) {
-  g_err.clear();
+  clear_error();
   return run(p, false, d_resid, d_coef, static_cast<cudaStream_t>(stream));
 }
 
 int adj_transform_fwd_f32(adj_plan_t* p, const float* d_x, float* d_coef, void* stream) {
-  g_err.clear();
+  clear_error();
   return run_fwd_f32(p, d_x, d_coef, static_cast<cudaStream_t>(stream));
 }
 
 int adj_transform_inv(adj_plan_t* p, const float* d_coef, float* d_resid_out, void* stream) {
-  g_err.clear();
+  clear_error();
   return run(p, true, d_coef, d_resid_out, static_cast<cudaStream_t>(stream));
 }
 
 int adj_plan_set_frame_blocks(adj_plan_t* p, const adj_frame_block_t* blocks, int64_t n_blocks, int32_t frame_w,
-                              int32_t frame_h, int32_t stride) {
-  g_err.clear();
+                              int32_t frame_h, int32_t stride) try {
+  clear_error();
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
   if (n_blocks < 0 || (n_blocks > 0 && !blocks)) return fail(ADJ_ERR_INVALID_ARG, "bad block list");
   if (frame_w <= 0 || frame_h <= 0 || frame_w % 4 || frame_h % 4)
@@ -1051,6 +1085,9 @@ int adj_plan_set_frame_blocks(adj_plan_t* p, const adj_frame_block_t* blocks, in
   if ((int64_t)stride * frame_h > (int64_t(1) << 34)) return fail(ADJ_ERR_INVALID_ARG, "frame too large");
   const int n_tfs = (int)p->tfs.size();
   const int gw = frame_w / 4, gh = frame_h / 4;
+  // disjoint blocks cover at least one 4 x 4 cell each
+  if (n_blocks > (int64_t)gw * gh)
+    return fail(ADJ_ERR_INVALID_ARG, "%lld blocks cannot fit in a %dx%d frame", (long long)n_blocks, frame_w, frame_h);
   std::vector<uint8_t> cover((size_t)gw * gh, 0);  // 4 x 4 cells already taken
   std::vector<adj_block_t> packed(n_blocks);
   std::vector<int64_t> foff(n_blocks);
@@ -1064,7 +1101,7 @@ int adj_plan_set_frame_blocks(adj_plan_t* p, const adj_frame_block_t* blocks, in
                   b.h, p->tfs[b.tf_h].n, p->tfs[b.tf_v].n);
     if (b.x < 0 || b.y < 0 || b.x % 4 || b.y % 4)
       return fail(ADJ_ERR_MISALIGNED, "block %lld at (%d, %d): positions must be non-negative multiples of 4", (long long)i, b.x, b.y);
-    if (b.x + b.w > frame_w || b.y + b.h > frame_h)
+    if ((int64_t)b.x + b.w > frame_w || (int64_t)b.y + b.h > frame_h)
       return fail(ADJ_ERR_INVALID_ARG, "block %lld at (%d, %d) leaves the %dx%d frame", (long long)i, b.x, b.y, frame_w, frame_h);
     for (int cy = b.y / 4; cy < (b.y + b.h) / 4; ++cy)
       for (int cx = b.x / 4; cx < (b.x + b.w) / 4; ++cx) {
@@ -1076,7 +1113,6 @@ int adj_plan_set_frame_blocks(adj_plan_t* p, const adj_frame_block_t* blocks, in
     foff[i] = (int64_t)b.y * stride + b.x;
     total += (int64_t)b.w * b.h;
   }
-  (void)gh;
   // the packed list is in storage order already (offsets increase with the list index)
   p->blocks = packed;
   p->orig.resize(n_blocks);
@@ -1094,23 +1130,26 @@ int adj_plan_set_frame_blocks(adj_plan_t* p, const adj_frame_block_t* blocks, in
   if (rc) return rc;
   p->has_blocks = true;
   return ADJ_OK;
+} catch (...) {
+  if (p) free_blocks(p);
+  return entry_exception();
 }
 
 int adj_transform_fwd_frame(adj_plan_t* p, const int16_t* d_frame, float* d_coef, void* stream) {
-  g_err.clear();
+  clear_error();
   return run_frame(p, false, d_frame, d_coef, false, static_cast<cudaStream_t>(stream));
 }
 
 int adj_transform_inv_frame(adj_plan_t* p, const float* d_coef, float* d_frame_f32, int16_t* d_frame_i16,
                             void* stream) {
-  g_err.clear();
+  clear_error();
   if (!!d_frame_f32 == !!d_frame_i16) return fail(ADJ_ERR_INVALID_ARG, "give exactly one of the FP32 and int16 outputs");
   if (d_frame_f32) return run_frame(p, true, d_coef, d_frame_f32, false, static_cast<cudaStream_t>(stream));
   return run_frame(p, true, d_coef, d_frame_i16, true, static_cast<cudaStream_t>(stream));
 }
 
-int adj_plan_prepare_multiple(adj_plan_t* p, int64_t* side_offsets, int64_t* side_total) {
-  g_err.clear();
+int adj_plan_prepare_multiple(adj_plan_t* p, int64_t* side_offsets, int64_t* side_total) try {
+  clear_error();
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
   if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
   if (p->frame) return fail(ADJ_ERR_INVALID_ARG, "the Multiple forward takes a packed block list, not frame blocks");
@@ -1146,56 +1185,63 @@ int adj_plan_prepare_multiple(adj_plan_t* p, int64_t* side_offsets, int64_t* sid
   if (side_offsets) std::copy(off.begin(), off.end(), side_offsets);
   if (side_total) *side_total = off.back();
   return ADJ_OK;
+} catch (...) {
+  if (p) free_blocks(p);
+  return entry_exception();
 }
 
 int adj_transform_fwd_multiple(adj_plan_t* p, const int16_t* d_resid, float* d_coef, float* d_side, void* stream) {
-  g_err.clear();
+  clear_error();
   return run_multi(p, d_resid, d_coef, d_side, static_cast<cudaStream_t>(stream));
 }
 
 int adj_transform_bwd(adj_plan_t* p, const void* d_x, int32_t x_dtype, const float* d_gy, float* d_gx,
                       float* d_gparams, void* stream) {
-  g_err.clear();
+  clear_error();
   if (x_dtype != ADJ_DTYPE_INT16 && x_dtype != ADJ_DTYPE_FP32) return fail(ADJ_ERR_INVALID_ARG, "x_dtype %d", x_dtype);
   return run_bwd(p, d_x, x_dtype == ADJ_DTYPE_FP32, d_gy, d_gx, d_gparams, static_cast<cudaStream_t>(stream));
 }
 
 int adj_plan_param_layout(const adj_plan_t* p, int32_t* offsets) {
-  g_err.clear();
+  clear_error();
   if (!p || !offsets) return fail(ADJ_ERR_INVALID_ARG, "null argument");
   for (size_t i = 0; i < p->g_off.size(); ++i) offsets[i] = p->g_off[i];
   return ADJ_OK;
 }
 
 int adj_transform_fwd_plain(adj_plan_t* p, const int16_t* d_resid, float* d_coef, void* stream) {
-  g_err.clear();
+  clear_error();
   return run_plain(p, false, d_resid, d_coef, static_cast<cudaStream_t>(stream));
 }
 
 int adj_transform_inv_plain(adj_plan_t* p, const float* d_coef, float* d_resid_out, void* stream) {
-  g_err.clear();
+  clear_error();
   return run_plain(p, true, d_coef, d_resid_out, static_cast<cudaStream_t>(stream));
 }
 
-int adj_transform_fwd_host(adj_plan_t* p, const int16_t* h_resid, float* h_coef, void* stream) {
-  g_err.clear();
+int adj_transform_fwd_host(adj_plan_t* p, const int16_t* h_resid, float* h_coef, void* stream) try {
+  clear_error();
   return run_host(p, false, h_resid, h_coef, static_cast<cudaStream_t>(stream));
+} catch (...) {
+  return entry_exception();
 }
 
-int adj_transform_inv_host(adj_plan_t* p, const float* h_coef, float* h_resid_out, void* stream) {
-  g_err.clear();
+int adj_transform_inv_host(adj_plan_t* p, const float* h_coef, float* h_resid_out, void* stream) try {
+  clear_error();
   return run_host(p, true, h_coef, h_resid_out, static_cast<cudaStream_t>(stream));
+} catch (...) {
+  return entry_exception();
 }
 
 int adj_plan_get_tuning(const adj_plan_t* p, adj_tuning_t* t) {
-  g_err.clear();
+  clear_error();
   if (!p || !t) return fail(ADJ_ERR_INVALID_ARG, "null argument");
   *t = p->tuning;
   return ADJ_OK;
 }
 
-int adj_plan_set_tuning(adj_plan_t* p, const adj_tuning_t* t) {
-  g_err.clear();
+int adj_plan_set_tuning(adj_plan_t* p, const adj_tuning_t* t) try {
+  clear_error();
   if (!p || !t) return fail(ADJ_ERR_INVALID_ARG, "null argument");
   for (int i = 0; i < 25; ++i)
     if (t->cap_div[i] != 1 && t->cap_div[i] != 2 && t->cap_div[i] != 4 && t->cap_div[i] != 8)
@@ -1206,6 +1252,9 @@ int adj_plan_set_tuning(adj_plan_t* p, const adj_tuning_t* t) {
   apply_grid(p);
   if (p->has_blocks) return build_layout(p);
   return ADJ_OK;
+} catch (...) {
+  if (p) free_blocks(p);
+  return entry_exception();
 }
 
 namespace {
@@ -1221,7 +1270,7 @@ uint64_t signature(const adj_plan* p) {
   for (uint64_t v : hist) {
     // quantise counts to ~3% so that equal workloads of other seeds share a tuning
     uint64_t q = v;
-    while (q >= 64) q = (q >> 1) | 0;  // keep the top bits
+    while (q >= 64) q >>= 1;  // keep the top bits
     uint64_t lg = 0;
     for (uint64_t t = v; t >= 64; t >>= 1) ++lg;
     const uint64_t key = (lg << 8) | q;
@@ -1302,8 +1351,8 @@ int time_plan(adj_plan* p, const int16_t* x, float* y, float* xr, cudaStream_t s
 }  // namespace
 
 int adj_plan_autotune(adj_plan_t* p, const int16_t* x, float* y, float* xr, const char* cache_path, int32_t max_evals,
-                      void* stream_) {
-  g_err.clear();
+                      void* stream_) try {
+  clear_error();
   if (!p) return fail(ADJ_ERR_INVALID_ARG, "null plan");
   if (!p->has_blocks) return fail(ADJ_ERR_NO_BLOCKS, "adj_plan_set_blocks has not been called");
   int rc;
@@ -1365,10 +1414,13 @@ int adj_plan_autotune(adj_plan_t* p, const int16_t* x, float* y, float* xr, cons
   if ((rc = adj_plan_set_tuning(p, &best))) return rc;
   cache_store(cache_path, dev, sig, best);
   return ADJ_OK;
+} catch (...) {
+  if (p) free_blocks(p);
+  return entry_exception();
 }
 
 int adj_plan_info(const adj_plan_t* p, adj_plan_info_t* info) {
-  g_err.clear();
+  clear_error();
   if (!p || !info) return fail(ADJ_ERR_INVALID_ARG, "null argument");
   info->n_blocks = p->n_blocks;
   info->total_coefs = p->total;

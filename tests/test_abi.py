@@ -6,6 +6,7 @@ import ctypes as C
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -52,8 +53,8 @@ def test_struct_layout_matches_c(tmp_path):
 int main(void) {{
   printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(adj_1d_desc_t), offsetof(adj_1d_desc_t, layer_parity),
          offsetof(adj_1d_desc_t, k), offsetof(adj_1d_desc_t, q), sizeof(adj_block_t), sizeof(adj_plan_info_t));
-  printf("%d %d %d %d %d %d\\n", ADJ_ERR_INVALID_ARG, ADJ_ERR_UNSUPPORTED_SIZE, ADJ_ERR_PARAM_MISMATCH,
-         ADJ_ERR_MISALIGNED, ADJ_ERR_CUDA, ADJ_ERR_NO_BLOCKS);
+  printf("%d %d %d %d %d %d %d\\n", ADJ_ERR_INVALID_ARG, ADJ_ERR_UNSUPPORTED_SIZE, ADJ_ERR_PARAM_MISMATCH,
+         ADJ_ERR_MISALIGNED, ADJ_ERR_CUDA, ADJ_ERR_NO_BLOCKS, ADJ_ERR_NO_MEMORY);
   return 0;
 }}""")
     exe = tmp_path / "layout"
@@ -62,8 +63,8 @@ int main(void) {{
     assert [int(x) for x in sizes.split()] == [
         C.sizeof(_lib.Adj1dDesc), _lib.Adj1dDesc.layer_parity.offset, _lib.Adj1dDesc.k.offset,
         _lib.Adj1dDesc.q.offset, _lib.BLOCK_DTYPE.itemsize, C.sizeof(_lib.AdjPlanInfo)]
-    assert [int(x) for x in codes.split()] == [-1, -2, -3, -4, -5, -6]
-    assert sorted(_lib.ERR_CODE.values()) == [-6, -5, -4, -3, -2, -1]
+    assert [int(x) for x in codes.split()] == [-1, -2, -3, -4, -5, -6, -7]
+    assert sorted(_lib.ERR_CODE.values()) == [-7, -6, -5, -4, -3, -2, -1]
 
 
 def _create(lib, tfs):
@@ -134,3 +135,34 @@ def test_generated_cores_are_current():
     text = g.generate()   # raises if a flow graph is off its definition
     with open(os.path.join(os.path.dirname(path), "cores_gen.cuh")) as f:
         assert f.read() == text
+
+
+_NO_MEMORY_SCRIPT = r"""
+import resource
+import numpy as np
+import synth
+import paper_2505_23618_gb300 as adj
+from paper_2505_23618_gb300 import _lib
+_lib.lib()
+n = 1 << 20
+blocks = np.zeros(n, dtype=synth.BLOCK_DTYPE)
+blocks["w"] = blocks["h"] = 4
+blocks["offset"] = np.arange(n) * 16
+vm = [int(l.split()[1]) * 1024 for l in open("/proc/self/status") if l.startswith("VmSize")][0]
+resource.setrlimit(resource.RLIMIT_AS, (vm + (4 << 20), resource.RLIM_INFINITY))
+try:
+    adj.layout_preview([synth.Tf(n=4, core=0)], blocks, n * 16)
+    print("no error")
+except adj.AdjError as e:
+    print(e.name)
+"""
+
+
+def test_host_allocation_failure_is_an_error_code():
+    """A failed host allocation inside the library comes back as ADJ_ERR_NO_MEMORY, not as a
+    C++ exception through the C ABI (which would abort the process).  The planner's tables
+    for a million blocks are built under an address-space limit 4 MiB above current use."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _NO_MEMORY_SCRIPT], cwd=root, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().splitlines()[-1] == "ADJ_ERR_NO_MEMORY"

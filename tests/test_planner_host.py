@@ -91,3 +91,28 @@ def test_preview_errors():
     assert e.value.name == "ADJ_ERR_INVALID_ARG"
     r = adj.layout_preview(tfs, blocks, 128, n_sm=4)
     assert len(r["tiles"]) == 1 and r["tiles"][0]["nblk"] == 2
+
+
+def test_preview_rejects_blocks_out_of_range():
+    tfs = [synth.Tf(n=8, core=0)]
+    one = np.zeros(1, dtype=synth.BLOCK_DTYPE)
+    one["w"] = one["h"] = 8
+    # an offset whose end would overflow a signed 64-bit sum is past the end, not wrapped around
+    one["offset"] = np.iinfo(np.int64).max - 15
+    with pytest.raises(adj.AdjError) as e:
+        adj.layout_preview(tfs, one, 1 << 20)
+    assert e.value.name == "ADJ_ERR_INVALID_ARG" and "extends past" in str(e.value)
+    one["offset"] = (1 << 20) - 48                   # ends 16 samples past total_coefs
+    with pytest.raises(adj.AdjError) as e:
+        adj.layout_preview(tfs, one, 1 << 20)
+    assert "extends past" in str(e.value)
+    one["offset"] = (1 << 20) - 64                   # ends exactly at total_coefs
+    assert len(adj.layout_preview(tfs, one, 1 << 20)["tiles"]) == 1
+    # more blocks than disjoint 16-sample blocks can fit is rejected before anything is read
+    many = np.zeros(5, dtype=synth.BLOCK_DTYPE)
+    many["w"] = many["h"] = 8
+    many["offset"] = np.arange(5) * 64
+    with pytest.raises(adj.AdjError) as e:
+        adj.layout_preview(tfs, many, 64)
+    assert e.value.name == "ADJ_ERR_INVALID_ARG" and "cannot fit" in str(e.value)
+    assert adj.layout_preview(tfs, many, 5 * 64)["tiles"]["nblk"].sum() == 5
