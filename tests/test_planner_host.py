@@ -116,3 +116,20 @@ def test_preview_rejects_blocks_out_of_range():
         adj.layout_preview(tfs, many, 64)
     assert e.value.name == "ADJ_ERR_INVALID_ARG" and "cannot fit" in str(e.value)
     assert adj.layout_preview(tfs, many, 5 * 64)["tiles"]["nblk"].sum() == 5
+
+
+@pytest.mark.parametrize("rows,name", [
+    (((0, 12, 8, 0, 0),), "ADJ_ERR_UNSUPPORTED_SIZE"),            # 12 is not a block side
+    (((0, 8, 8, 0, 5),), "ADJ_ERR_INVALID_ARG"),                  # transform index out of range
+    (((0, 8, 16, 0, 0),), "ADJ_ERR_PARAM_MISMATCH"),              # 16 rows, 8-point transform
+    (((8, 8, 8, 0, 0),), "ADJ_ERR_MISALIGNED"),                   # offset not a multiple of 16
+    (((-16, 8, 8, 0, 0),), "ADJ_ERR_MISALIGNED"),                 # negative offset
+    (((0, 8, 8, 0, 0), (48, 8, 8, 0, 0)), "ADJ_ERR_INVALID_ARG"), # overlap
+    (((4064, 8, 8, 0, 0),), "ADJ_ERR_INVALID_ARG"),               # past total_coefs
+])
+def test_block_validation_codes(rows, name):
+    """adj_layout_preview runs the same block validation as adj_plan_set_blocks."""
+    tfs = [synth.Tf(n=8, core=0), synth.Tf(n=16, core=1)]
+    with pytest.raises(adj.AdjError) as e:
+        adj.layout_preview(tfs, np.array(list(rows), dtype=synth.BLOCK_DTYPE), 4096)
+    assert e.value.name == name
