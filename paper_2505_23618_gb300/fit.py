@@ -106,10 +106,20 @@ def cayley_grad(w, k, dg, gq):
 
 
 def cayley_init(q):
-    """(w, dg) with Dg Cayley(W) = q for an orthogonal q whose Dg q has no eigenvalue -1."""
+    """(w, dg) with Dg Cayley(W) = q for an orthogonal q.
+
+    The Cayley map reaches the orthogonal matrices of determinant +1 without an eigenvalue -1.
+    An orthogonal matrix of determinant -1 always has the eigenvalue -1, so the signs Dg are
+    chosen to make det(Dg q) = +1: first so that Dg q has a non-negative diagonal (as close to I
+    as the diagonal allows), then, if the determinant is still -1, flipping the row whose
+    diagonal entry is smallest in magnitude.  (A determinant +1 matrix with the eigenvalue -1,
+    a rotation by exactly pi in some plane, is not handled; it does not arise from a generic
+    start.)"""
     k = q.shape[0]
-    # choose the signs so that Dg q is as close to I as the diagonal allows
     dg = np.where(np.diag(q) < 0, -1.0, 1.0)
+    if np.linalg.det(dg[:, None] * q) < 0:
+        i = int(np.argmin(np.abs(np.diag(q))))
+        dg[i] = -dg[i]
     C0 = dg[:, None] * q
     I = np.eye(k)
     W = np.linalg.solve(I + C0, I - C0)   # inverse Cayley map
