@@ -48,9 +48,9 @@ def parse():
     p.add_argument("--frames", type=int, default=8, help="frames of the workload (profiling uses fewer)")
     p.add_argument("--autotune", type=int, default=48, help="autotuner evaluations before timing (0: off)")
     p.add_argument("--no-multiple", action="store_true", help="skip the Multiple-forward measurement")
-    p.add_argument("--config5", dest="config5", action="store_true", default=True,
+    p.add_argument("--uhd8k", dest="uhd8k", action="store_true", default=True,
                    help="measure the large-frame workload (default)")
-    p.add_argument("--no-config5", dest="config5", action="store_false")
+    p.add_argument("--no-uhd8k", dest="uhd8k", action="store_false")
     p.add_argument("--no-frame", action="store_true", help="skip the frame-layout measurement")
     p.add_argument("--classes", action="store_true",
                    help="diagnostic: time uniform single-class workloads (one JSON line per class) instead")
@@ -67,7 +67,7 @@ def dist_env():
 def workload(rank=0, frames=8):
     import synth
     # every rank transforms its own seeded batch of the same shape (weak scaling)
-    return synth.config3(seed=3 + 1000 * rank, frames=frames)
+    return synth.uhd_mixed(seed=3 + 1000 * rank, frames=frames)
 
 
 def aggregate_max(t_local, device=None):
@@ -217,7 +217,7 @@ def cpu_baseline(sample_desc="full workload (66.4 M coefficients), one forward +
     code = (
         "import time, json, sys; sys.path.insert(0, %r)\n"
         "import numpy as np, synth, oracle\n"
-        "wl = synth.config3()\n"
+        "wl = synth.uhd_mixed()\n"
         "t = time.perf_counter(); y = oracle.forward_blocks(wl.data, wl.blocks, wl.tfs)\n"
         "x = oracle.inverse_blocks(y, wl.blocks, wl.tfs); dt = time.perf_counter() - t\n"
         "print(json.dumps({'coefs': int(wl.total), 'seconds': dt}))\n" % ROOT)
@@ -278,7 +278,7 @@ def bench_multiple(args, rank, dev, stream, flush, peak):
     import synth
     import paper_2505_23618_gb300 as adj
 
-    wl = synth.config3_multiple(seed=3 + 1000 * rank, frames=args.frames)
+    wl = synth.uhd_mixed_multiple(seed=3 + 1000 * rank, frames=args.frames)
     coefs, nb = wl.total, int(wl.blocks.size)
     reps = max(3, min(args.steps, 30))
     x = torch.from_numpy(wl.data).to(dev)
@@ -330,7 +330,7 @@ def bench_multiple(args, rank, dev, stream, flush, peak):
 FITTED = os.path.join(ROOT, "paper_2505_23618_gb300", "params", "fitted.json")
 
 
-def config5_tfs():
+def uhd8k_tfs():
     """The large-frame workload's transforms: fitted DST-7 / DCT-8 approximations when the
     fitted parameter file is present (horizontal DST-3 + 12-layer band; vertical DCT-2 + post
     with the DCT-8 block S Q S of Eq. 5), else None (the workload's seeded parameters)."""
@@ -350,7 +350,7 @@ def config5_tfs():
         return None, None, "seeded"
 
 
-def bench_config5(args, rank, dev, stream, flush, peak):
+def bench_uhd8k(args, rank, dev, stream, flush, peak):
     """Large-frame workload (16 frames of 7680x4320, 64x64 and 64x32 blocks; horizontal
     DST-7 approximation, vertical DCT-8 approximation): fused forward + inverse, and the exact
     dense DST-7 / DCT-8 product on the same blocks as context.  Median of L2-flushed repeats."""
@@ -361,8 +361,8 @@ def bench_config5(args, rank, dev, stream, flush, peak):
     import paper_2505_23618_gb300 as adj
     from paper_2505_23618_gb300 import targets
 
-    h_tf, v_tfs, src = config5_tfs()
-    wl = synth.config5(seed=5 + 1000 * rank, h_tf=h_tf, v_tfs=v_tfs)
+    h_tf, v_tfs, src = uhd8k_tfs()
+    wl = synth.uhd8k(seed=5 + 1000 * rank, h_tf=h_tf, v_tfs=v_tfs)
     coefs, nb = wl.total, int(wl.blocks.size)
     reps = max(3, min(args.steps, 10))
     x = torch.from_numpy(wl.data).to(dev)
@@ -403,7 +403,7 @@ def bench_config5(args, rank, dev, stream, flush, peak):
                 "fwd_frac": round(bf / (tf * 1e-3) / 1e9 / peak, 4), "inv_frac": round(bi / (ti * 1e-3) / 1e9 / peak, 4),
                 "flops_per_coef": round(fl / coefs, 2), "alu_fwd": alu_roofline(fl, tf), "alu_inv": alu_roofline(fl, ti),
                 "algorithmic_bytes": {"fwd": bf, "inv": bi},
-                "traffic": {"fwd": profiled_traffic("config5_fwd"), "inv": profiled_traffic("config5_inv")},
+                "traffic": {"fwd": profiled_traffic("uhd8k_fwd"), "inv": profiled_traffic("uhd8k_inv")},
                 "roundtrip_max_abs_err": rt})
     # the exact transforms the adjustments stand in for, as dense products (Eq. 3)
     dense = [targets.dense_tf(targets.dst7(64)), targets.dense_tf(targets.dct8(64)), targets.dense_tf(targets.dct8(32))]
@@ -420,8 +420,9 @@ def bench_config5(args, rank, dev, stream, flush, peak):
 
 def bench_frame(args, rank, dev, stream, flush, peak):
     """Blocks inside frames (no packing step): forward from an int16 residual frame and inverse
-    back into an int16 frame (rounded), on 8 frames of 3840x2160 tiled as in config 3 and
-    stacked into one frame (one launch per direction), median of L2-flushed repeats."""
+    back into an int16 frame (rounded), on 8 frames of 3840x2160 tiled like the mixed UHD
+    workload and stacked into one frame (one launch per direction), median of L2-flushed
+    repeats."""
     import numpy as np
     import torch
 
@@ -430,7 +431,7 @@ def bench_frame(args, rank, dev, stream, flush, peak):
 
     reps = max(3, min(args.steps, 20))
     n_frames = max(1, args.frames)
-    frame, blocks, tfs = synth.config3_frame(seed=3 + 1000 * rank, frames=n_frames)
+    frame, blocks, tfs = synth.uhd_mixed_frame(seed=3 + 1000 * rank, frames=n_frames)
     plan = adj.Plan(tfs)
     plan.set_frame_blocks(blocks, 3840, frame.shape[0], frame.shape[1])
     x = torch.from_numpy(frame).to(dev)
@@ -455,7 +456,7 @@ def bench_frame(args, rank, dev, stream, flush, peak):
     tf = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
     ti = float(np.median([e[2].elapsed_time(e[3]) for e in ev]))
     plan.close()
-    return {"workload": f"{n_frames} frames 3840x2160 (config-3 tiling) stacked, int16 frame in, int16 frame out",
+    return {"workload": f"{n_frames} frames 3840x2160 (mixed 4-64 tiling) stacked, int16 frame in, int16 frame out",
             "value": round(coefs / ((tf + ti) * 1e-3) / 1e9, 3), "unit": UNIT, "fwd_ms": round(tf, 4),
             "inv_ms": round(ti, 4), "fwd_frac": round(coefs * 6 / (tf * 1e-3) / 1e9 / peak, 4),
             "inv_frac": round(coefs * 6 / (ti * 1e-3) / 1e9 / peak, 4),
@@ -562,7 +563,7 @@ def run_fused(args):
 
     peak, peak_src = measured_peak()
     multiple = bench_multiple(args, rank, dev, stream, flush, peak) if not args.no_multiple else None
-    config5 = bench_config5(args, rank, dev, stream, flush, peak) if args.config5 else None
+    uhd8k = bench_uhd8k(args, rank, dev, stream, flush, peak) if args.uhd8k else None
     frame = bench_frame(args, rank, dev, stream, flush, peak) if not args.no_frame else None
 
     # end to end through the host-buffer C-ABI calls (pinned memory), copies included
@@ -620,7 +621,7 @@ def run_fused(args):
                       "roundtrip_max_abs_err": plain_rt},
             "roofline": roof,
             "multiple": multiple,
-            "config5": config5,
+            "uhd8k": uhd8k,
             "frame": frame,
             "kernels": {k: {"ms": round(v["ms"], 4), "GB/s": round(v["gbs"], 1), "frac": round(v["frac"], 4)}
                         for k, v in kern.items()},

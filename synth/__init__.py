@@ -136,7 +136,7 @@ def _stats_c2(rng, nb):
             np.exp(3.0 + rng.standard_normal(nb)))
 
 
-def config1(seed: int = 1) -> Workload:
+def blocks32_band(seed: int = 1) -> Workload:
     """1024 blocks 32x32, rho=0.95, sigma=40, clip 255; DCT-2 + 2-layer band both ways."""
     rng = np.random.default_rng(seed)
     tfs = [random_band(rng, 32, CORE_DCT2, [0, 1]),   # horizontal
@@ -147,11 +147,11 @@ def config1(seed: int = 1) -> Workload:
     blocks["offset"] = np.arange(nb, dtype=np.int64) * 1024
     blocks["w"] = blocks["h"] = 32
     blocks["tf_h"], blocks["tf_v"] = 0, 1
-    return Workload("config1-1024x32x32-dct2-band2", blocks, data, tfs, 255,
+    return Workload("1024x32x32-dct2-band2", blocks, data, tfs, 255,
                     "1024 32x32 AR(1) rho=.95 sigma=40; DCT-2 + 2-layer band, both directions")
 
 
-def config2(seed: int = 2, per_size: int = 2048) -> Workload:
+def blocks32_64_mixed(seed: int = 2, per_size: int = 2048) -> Workload:
     """2048 x 32x32 + 2048 x 64x64, 10-bit; H: DST-3 + 4-layer band; V: DCT-2 + post K=N/2."""
     rng = np.random.default_rng(seed)
     tfs = []
@@ -165,7 +165,7 @@ def config2(seed: int = 2, per_size: int = 2048) -> Workload:
     th = np.array([ids[("h", int(x))] for x in w])
     tv = np.array([ids[("v", int(x))] for x in w])
     blocks, data = _pack((w, w, th, tv), rng, _stats_c2, 1023)
-    return Workload(f"config2-{per_size}x32x32+{per_size}x64x64-dst3band4-dct2post", blocks,
+    return Workload(f"{per_size}x32x32+{per_size}x64x64-dst3band4-dct2post", blocks,
                     data, tfs, 1023,
                     "2048x32x32 + 2048x64x64 10-bit AR(1), rho~U[.6,.99], sigma~logN(3,1); "
                     "H DST-3 + 4-layer band, V DCT-2 + post K=N/2")
@@ -224,7 +224,7 @@ def _ctu_sizes(rng, frames: int, width: int, height: int):
     return np.array(ws), np.array(hs)
 
 
-def config3(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 2160) -> Workload:
+def uhd_mixed(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 2160) -> Workload:
     """Frames tiled into CTUs of 64x64 with per-CTU block sizes (``_ctu_sizes``),
     per-block types: each block draws its horizontal and vertical (core, kind)
     uniformly from the 12 combinations.
@@ -244,7 +244,7 @@ def config3(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 216
     th = lut_h[w, ch, kh]
     tv = lut_v[h, cv, kv]
     blocks, data = _pack((w, h, th, tv), rng, _stats_c2, 1023)
-    return Workload(f"config3-mixed-{frames}x{width}x{height}", blocks, data, tfs, 1023,
+    return Workload(f"mixed4-64-{frames}x{width}x{height}", blocks, data, tfs, 1023,
                     f"{frames} frames {width}x{height} tiled by per-CTU sizes 4..64, "
                     "per-block core x adjustment in each direction, 10-bit AR(1)")
 
@@ -254,7 +254,7 @@ FRAME_BLOCK_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("w", "<u2"), ("h", "<
 
 
 def ctu_frame_blocks(rng, width: int, height: int):
-    """Positions and sizes of the blocks of one frame tiled like config 3 (``_ctu_sizes``):
+    """Positions and sizes of the blocks of one frame tiled like the mixed UHD workload (``_ctu_sizes``):
     (x, y, w, h) arrays, CTUs in raster order, blocks in raster order inside a CTU region."""
     cols = width // 64
     full_rows, rem = divmod(height, 64)
@@ -285,11 +285,11 @@ def ctu_frame_blocks(rng, width: int, height: int):
     return np.array(xs), np.array(ys), np.array(ws), np.array(hs)
 
 
-def config3_frame(seed: int = 3, width: int = 3840, height: int = 2160, stride: int | None = None,
-                  frames: int = 1):
-    """Config-3 frames in frame layout: (frame int16 [frames * height, stride], frame blocks, tfs).
+def uhd_mixed_frame(seed: int = 3, width: int = 3840, height: int = 2160, stride: int | None = None,
+                    frames: int = 1):
+    """Mixed UHD frames in frame layout: (frame int16 [frames * height, stride], frame blocks, tfs).
 
-    The blocks tile each frame as in config 3 (per-CTU sizes, per-block core x adjustment in
+    The blocks tile each frame as in ``uhd_mixed`` (per-CTU sizes, per-block core x adjustment in
     each direction, 10-bit AR(1) residual per block); ``stride`` (default: width rounded up to
     a multiple of 64) leaves unused samples at the end of every row.  Several frames are
     stacked one below the other, which makes them one taller frame with the same stride."""
@@ -322,12 +322,12 @@ def config3_frame(seed: int = 3, width: int = 3840, height: int = 2160, stride: 
     return frame, blocks, tfs
 
 
-def config3_multiple(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 2160,
-                     k_max: int = 8) -> Workload:
-    """The config-3 frame tiling for the encoder's DST-7 / DCT-8 search (Section 2.3):
+def uhd_mixed_multiple(seed: int = 3, frames: int = 8, width: int = 3840, height: int = 2160,
+                       k_max: int = 8) -> Workload:
+    """The mixed UHD frame tiling for the encoder's DST-7 / DCT-8 search (Section 2.3):
     every block uses, in each direction, a DCT-2 with a post-adjustment of size
     K = min(k_max, n/2) (the 8 x 8 adjustment at 16 points and more), Q Haar-random per
-    (direction, n).  Same residual statistics as config 3."""
+    (direction, n).  Same residual statistics as ``uhd_mixed``."""
     rng = np.random.default_rng(seed)
     tfs, lut = [], {}
     for d in ("h", "v"):
@@ -338,13 +338,13 @@ def config3_multiple(seed: int = 3, frames: int = 8, width: int = 3840, height: 
     th = np.array([lut["h", int(x)] for x in SIZES])[np.log2(w).astype(int) - 2]
     tv = np.array([lut["v", int(x)] for x in SIZES])[np.log2(h).astype(int) - 2]
     blocks, data = _pack((w, h, th, tv), rng, _stats_c2, 1023)
-    return Workload(f"config3-multiple-{frames}x{width}x{height}", blocks, data, tfs, 1023,
+    return Workload(f"mixed4-64-multiple-{frames}x{width}x{height}", blocks, data, tfs, 1023,
                     f"{frames} frames {width}x{height} tiled by per-CTU sizes 4..64, DCT-2 + "
                     f"K=min({k_max}, n/2) post-adjustment both ways, 10-bit AR(1)")
 
 
-def config5(seed: int = 5, frames: int = 16, width: int = 7680, height: int = 4320,
-            h_tf: Tf | None = None, v_tfs: dict | None = None) -> Workload:
+def uhd8k(seed: int = 5, frames: int = 16, width: int = 7680, height: int = 4320,
+          h_tf: Tf | None = None, v_tfs: dict | None = None) -> Workload:
     """All 64x64 / 64x32 blocks; H: DST-3 + band at 64, V: DCT-2 + post (K=32 @64, 16 @32).
 
     Each full CTU is one 64x64 block or, with probability 1/2, two 64x32; the
@@ -373,7 +373,7 @@ def config5(seed: int = 5, frames: int = 16, width: int = 7680, height: int = 43
     th = np.zeros_like(h)
     tv = np.where(h == 64, 1, 2)
     blocks, data = _pack((w, h, th, tv), rng, _stats_c2, 1023)
-    return Workload(f"config5-{frames}x{width}x{height}-64x64+64x32", blocks, data, tfs, 1023,
+    return Workload(f"64x64+64x32-{frames}x{width}x{height}", blocks, data, tfs, 1023,
                     f"{frames} frames {width}x{height}, 64x64 and 64x32 blocks; H DST-3 + "
                     "12-layer band, V DCT-2 + post K=N/2, 10-bit AR(1)")
 

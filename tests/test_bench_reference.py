@@ -27,7 +27,7 @@ def test_reference_line():
     assert (j["n_gpus"], j["steps"], j["warmup"]) == (1, 2, 1)
     assert abs(j["ms_per_step"] - j["config"]["coefs"] / j["value"] / 1e6) <= 1e-6 * j["ms_per_step"]
     assert j["vs_baseline"] is None and j["data"] == "synthetic" and j["dtype"] == "f64"
-    assert j["config"]["workload"].startswith("config3")
+    assert j["config"]["workload"].startswith("mixed4-64-")
     cb = j["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == j["value"]
     e2e = j["e2e"]

@@ -96,11 +96,11 @@ def test_frame_matches_oracle(seed):
     check(frame, blocks, tfs, y, rf, ri, sentinel)
 
 
-def test_frame_full_size_config3():
-    """A 3840x2160 frame tiled as in config 3 (62,151 blocks, every block its own core x
+def test_frame_full_size_uhd_mixed():
+    """A 3840x2160 frame tiled like the mixed UHD workload (62,151 blocks, every block its own core x
     adjustment per direction): the int16 round trip is exact everywhere, and sampled blocks
     match the oracle."""
-    frame, blocks, tfs = synth.config3_frame()
+    frame, blocks, tfs = synth.uhd_mixed_frame()
     fh, stride = frame.shape
     y, rf, ri, sentinel = run_frame(frame, blocks, tfs, 3840, fh, stride)
     assert np.array_equal(ri[:, :3840], frame[:, :3840])

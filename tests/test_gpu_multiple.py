@@ -259,7 +259,7 @@ def test_multiple_full_size_sampled():
     configuration, checked against the oracle on a sample of blocks."""
     import torch
     import paper_2505_23618_gb300 as adj
-    wl = synth.config3_multiple()
+    wl = synth.uhd_mixed_multiple()
     with adj.Plan(wl.tfs) as plan:
         plan.set_blocks(wl.blocks, wl.total)
         off = plan.prepare_multiple()

@@ -54,13 +54,13 @@ def full_check(wl):
     return worst, rt
 
 
-def test_config1_full():
-    worst, rt = full_check(synth.config1())
+def test_blocks32_band_full():
+    worst, rt = full_check(synth.blocks32_band())
     assert worst < REL_TOL and rt < RT_TOL
 
 
-def test_config2_full():
-    worst, rt = full_check(synth.config2())
+def test_blocks32_64_mixed_full():
+    worst, rt = full_check(synth.blocks32_64_mixed())
     assert worst < REL_TOL and rt < RT_TOL
 
 
@@ -228,7 +228,7 @@ def test_host_path_chunked_matches_device_path():
     at every block sample."""
     import torch
     import paper_2505_23618_gb300 as adj
-    wl = synth.config3(frames=1)
+    wl = synth.uhd_mixed(frames=1)
     rng = np.random.default_rng(2)
     blocks = wl.blocks.copy()
     blocks = blocks[rng.random(blocks.size) < 0.8]           # leave gaps
@@ -259,7 +259,7 @@ def test_update_params_changes_result():
     import torch
     import paper_2505_23618_gb300 as adj
     rng = np.random.default_rng(4)
-    wl = synth.config1()
+    wl = synth.blocks32_band()
     new = [synth.random_band(rng, 32, 0, [0, 1]), synth.random_band(rng, 32, 0, [0, 1])]
     with adj.Plan(wl.tfs) as plan:
         plan.set_blocks(wl.blocks, wl.total)
@@ -344,9 +344,9 @@ def _full_size(wl, n_sample, seed):
     return check_forward(ys, sub)
 
 
-def test_config3_full_size_sampled():
-    assert _full_size(synth.config3(), 3000, 3) <= REL_TOL
+def test_uhd_mixed_full_size_sampled():
+    assert _full_size(synth.uhd_mixed(), 3000, 3) <= REL_TOL
 
 
-def test_config5_full_size_sampled():
-    assert _full_size(synth.config5(), 1500, 5) <= REL_TOL
+def test_uhd8k_full_size_sampled():
+    assert _full_size(synth.uhd8k(), 1500, 5) <= REL_TOL

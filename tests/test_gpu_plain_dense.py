@@ -24,7 +24,7 @@ def run(wl, plain):
         return y.cpu().numpy().astype(np.float64), xr.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("make", [synth.config1, synth.config2, lambda: synth.random_small(3, 500),
+@pytest.mark.parametrize("make", [synth.blocks32_band, synth.blocks32_64_mixed, lambda: synth.random_small(3, 500),
                                   lambda: synth.random_small(4, 37)])
 def test_plain_form_parity(make):
     wl = make()
@@ -63,9 +63,9 @@ def test_dense_reference_transform(plain):
 
 
 def test_adjusted_vs_dense_context_blocks():
-    """Config-5-like blocks transformed by adjusted DST-3/DCT-2 pairs and by the exact
+    """8K-workload-like blocks transformed by adjusted DST-3/DCT-2 pairs and by the exact
     DST-7 / DCT-8: both match the oracle on the same blocks."""
-    wl = synth.config5(frames=1, width=512, height=4320 - 64 * 60)
+    wl = synth.uhd8k(frames=1, width=512, height=4320 - 64 * 60)
     y, xr = run(wl, plain=False)
     check_forward(y, wl)
     tfs = [synth.Tf(n=64, core=0, kind=synth.KIND_DENSE, q=targets.dst7(64)),
@@ -106,7 +106,7 @@ def test_autotune_and_tuning_roundtrip(tmp_path):
     """The autotuner picks a tuning that keeps results identical; the cache replays it."""
     import torch
     import paper_2505_23618_gb300 as adj
-    wl = synth.config3(frames=1, width=1280, height=720)
+    wl = synth.uhd_mixed(frames=1, width=1280, height=720)
     with adj.Plan(wl.tfs) as plan:
         plan.set_blocks(wl.blocks, wl.total)
         x = torch.from_numpy(wl.data).cuda()

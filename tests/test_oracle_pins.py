@@ -283,9 +283,9 @@ def test_ar1_statistics():
 
 
 def test_workload_layouts():
-    wl = synth.config1()
+    wl = synth.blocks32_band()
     assert wl.total == 1024 * 1024 and wl.blocks.size == 1024
-    wl3 = synth.config3(frames=1, width=640, height=2160 - 64 * 27)
+    wl3 = synth.uhd_mixed(frames=1, width=640, height=2160 - 64 * 27)
     off = wl3.blocks["offset"]
     sz = wl3.blocks["w"].astype(np.int64) * wl3.blocks["h"]
     assert np.all(off[1:] == off[:-1] + sz[:-1]) and off[-1] + sz[-1] == wl3.total

@@ -15,7 +15,7 @@ def capacity(w, h):
 
 @pytest.fixture(scope="module")
 def mixed():
-    wl = synth.config3(seed=3, frames=2)
+    wl = synth.uhd_mixed(seed=3, frames=2)
     return wl, adj.layout_preview(wl.tfs, wl.blocks, wl.total, n_sm=152)
 
 
