@@ -124,8 +124,10 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
  * non-overlap; groups blocks of equal (w, h, tf_h, tf_v) into shared-memory tiles in
  * storage order, sorts the tiles by the code they run and cuts them into one scheduling
  * range per SM of about equal estimated run time (most expensive tiles first in each),
- * and uploads the tile list.  May be called again to replace the list.
- * Errors: INVALID_ARG, UNSUPPORTED_SIZE, PARAM_MISMATCH, MISALIGNED, CUDA.
+ * and uploads the tile list.  May be called again to replace the list; the previous
+ * list's device tables are freed then, so no launch of this plan may still be running.
+ * A list with more blocks than total_coefs / 16 is rejected before it is read.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, PARAM_MISMATCH, MISALIGNED, CUDA, NO_MEMORY.
  */
 int adj_plan_set_blocks(adj_plan_t* plan, const adj_block_t* blocks, int64_t n_blocks,
                         int64_t total_coefs);
@@ -155,9 +157,12 @@ int adj_layout_preview(const adj_1d_desc_t* tfs, int32_t n_tfs, const adj_block_
 
 /*
  * Replace the parameter values (angles, Q) of all transforms without changing their
- * structure (n, core, kind, layer parities, K).  Asynchronous on the legacy stream
- * ordering of cudaMemcpy: completes before it returns.
- * Errors: INVALID_ARG, PARAM_MISMATCH, CUDA.
+ * structure (n, core, kind, layer parities, K).  The upload is a synchronous cudaMemcpy
+ * that has completed when the call returns.  It is ordered after earlier work on the
+ * legacy default stream and on blocking streams only: launches of this plan on a
+ * non-blocking stream must have finished before the call (synchronise that stream).
+ * After a validation error the plan keeps its previous values.
+ * Errors: INVALID_ARG, PARAM_MISMATCH, CUDA, NO_MEMORY.
  */
 int adj_plan_update_params(adj_plan_t* plan, const adj_1d_desc_t* tfs, int32_t n_tfs);
 
