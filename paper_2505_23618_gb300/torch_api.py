@@ -138,10 +138,13 @@ def _make_autograd():
                 raise ValueError(f"params must be a vector of {_layout(plan)[-1]} entries (param_vector layout)")
             vals = params.detach().to("cpu", torch.float64).numpy()
             cur = getattr(plan, "_param_values", None)
+            s = torch.cuda.current_stream(x.device)
             if cur is None or cur.shape != vals.shape or not np.array_equal(cur, vals):
+                # the upload is not ordered after launches on a non-blocking stream: let the
+                # plan's earlier launches on this stream finish before their tables change
+                s.synchronize()
                 _set_params(plan, vals)
             y = torch.zeros(plan.total, dtype=torch.float32, device=x.device)
-            s = torch.cuda.current_stream(x.device)
             if x.dtype == torch.int16:
                 plan.fwd(x, y, s)
             else:
@@ -155,6 +158,7 @@ def _make_autograd():
             (x,) = ctx.saved_tensors
             plan = ctx.plan
             if not np.array_equal(plan._param_values, ctx.vals):
+                torch.cuda.current_stream(x.device).synchronize()
                 _set_params(plan, ctx.vals)
             need_x, need_p = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
             gx = torch.zeros(plan.total, dtype=torch.float32, device=x.device) if need_x else None
