@@ -120,7 +120,7 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
 
 /*
  * Give the plan its block list (host memory, n_blocks records) for buffers of
- * total_coefs samples.  Validates sizes, transform indices, alignment, bounds and
+ * total_coefs samples: the W x H residual blocks a codec transforms (Section 2.2).  Validates sizes, transform indices, alignment, bounds and
  * non-overlap; groups blocks of equal (w, h, tf_h, tf_v) into shared-memory tiles in
  * storage order, sorts the tiles by the code they run and cuts them into one scheduling
  * range per SM of about equal estimated run time (most expensive tiles first in each),
@@ -168,14 +168,19 @@ int adj_plan_update_params(adj_plan_t* plan, const adj_1d_desc_t* tfs, int32_t n
 
 /*
  * Forward 2-D transform of every block: d_resid (int16, device, total_coefs samples,
- * 16-B aligned) -> d_coef (FP32, device, total_coefs, 16-B aligned), Y = H_v X H_h^T.
- * Samples outside every block are not written.  One persistent kernel launch.
+ * 16-B aligned) -> d_coef (FP32, device, total_coefs, 16-B aligned), Y = H_v X H_h^T with
+ * H = C B A of Eq. 1 in each direction, applied horizontally and vertically to the whole
+ * block (Section 2.2).  Samples outside every block are not written.  One persistent
+ * kernel launch, asynchronous on `stream`.
+ * Errors: INVALID_ARG, NO_BLOCKS, MISALIGNED, CUDA.
  */
 int adj_transform_fwd(adj_plan_t* plan, const int16_t* d_resid, float* d_coef, void* stream);
 
 /*
  * Inverse 2-D transform: d_coef (FP32, device) -> d_resid_out (FP32, device, not
- * rounded), X = H_v^T Y H_h.  Same layout and alignment rules as adj_transform_fwd.
+ * rounded), X = H_v^T Y H_h: every factor of Eq. 1 is orthogonal, so H^-1 = A^T B^T C^T
+ * (the inverse core, the transposed post block, the band layers reversed with -theta).
+ * Same layout, alignment, launch and error rules as adj_transform_fwd.
  */
 int adj_transform_inv(adj_plan_t* plan, const float* d_coef, float* d_resid_out, void* stream);
 
