@@ -133,3 +133,10 @@ def test_block_validation_codes(rows, name):
     with pytest.raises(adj.AdjError) as e:
         adj.layout_preview(tfs, np.array(list(rows), dtype=synth.BLOCK_DTYPE), 4096)
     assert e.value.name == name
+
+
+def test_preview_of_an_empty_list():
+    r = adj.layout_preview([synth.Tf(n=8, core=0)], np.zeros(0, dtype=synth.BLOCK_DTYPE), 0)
+    assert r["tiles"].size == 0 and r["costs"].size == 0
+    assert list(r["range_begin"]) == [0]
+    assert not r["list"].any()             # only the spare entries the kernel may over-read
