@@ -332,19 +332,24 @@ int adj_transform_inv_host(adj_plan_t* plan, const float* h_coef, float* h_resid
  * Computes the same transform as adj_transform_fwd with the same fused kernel, for
  * n_blocks blocks of tf_v->n rows x tf_h->n columns stored back to back (block b starts
  * at sample b * w * h), all using tf_h horizontally and tf_v vertically.  d_resid (int16)
- * and d_coef (FP32) are caller-owned device buffers, 16-B aligned.  Asynchronous on
- * `stream` like adj_transform_fwd.
+ * and d_coef (FP32) are caller-owned device buffers, 16-B aligned.  The transform runs
+ * asynchronously on `stream`, but the transform records and parameters are uploaded from
+ * pageable host memory that lives only for the call, so the call may block the host until
+ * the work already queued on `stream` has finished (adj_transform_fwd, whose parameters
+ * were uploaded at plan creation, does not).  For the same reason the call cannot be
+ * recorded into a CUDA graph: while `stream` is capturing it returns INVALID_ARG and
+ * enqueues nothing.
  *
  * Scratch: the work counter, the two transform records, their FP32 parameters and the
  * tile list live in one static device array of ADJ_NOALLOC_SCRATCH_BYTES that every
  * device loading the library holds until the process exits.  No cudaMalloc, cudaFree or
  * other allocating routine is called.  The first call on a device (with that device
  * current) looks up the array's device address once; make that first call before any
- * stream capture.  Every call shares the array: it clears the work counter and rewrites
+ * stream capture on that device.  Every call shares the array: it clears the work counter and rewrites
  * the rest, and calls that overlap on the GPU (other streams or host threads) race on it,
  * so the caller must serialise them.
- * Errors: INVALID_ARG, UNSUPPORTED_SIZE (also n_blocks > ADJ_NOALLOC_MAX_BLOCKS),
- * PARAM_MISMATCH, MISALIGNED, CUDA.
+ * Errors: INVALID_ARG (also a call on a capturing stream), UNSUPPORTED_SIZE (also
+ * n_blocks > ADJ_NOALLOC_MAX_BLOCKS), PARAM_MISMATCH, MISALIGNED, CUDA.
  */
 #define ADJ_NOALLOC_SCRATCH_BYTES (3u << 20)
 #define ADJ_NOALLOC_MAX_BLOCKS 131072

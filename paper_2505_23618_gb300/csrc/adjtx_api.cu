@@ -126,7 +126,8 @@ struct adj_plan {
   std::vector<int64_t> frame_off;
   uint32_t* d_tile_side = nullptr;     // side or frame offset / 4, parallel to d_tile_blk
   int occ_multi = 0, grid_multi = 0;
-  int occ_frame = 0, grid_frame = 0;
+  int occ_frame = 0, grid_frame = 0;          // frame inverses (FP32 and int16 output)
+  int occ_frame_fwd = 0, grid_frame_fwd = 0;  // frame forward
   int occ_f32 = 0, grid_f32 = 0;      // forward of FP32 blocks
   adj_tuning_t tuning{};
   int occ_fwd = 0, occ_inv = 0;        // resident CTAs per SM of the fused kernels
@@ -393,7 +394,7 @@ int run_frame(adj_plan* p, bool inverse, const void* in, void* out, bool i16, cu
   a.n_ranges = p->n_ranges;
   a.tile_aux = p->d_tile_side;
   a.frame_stride = p->frame_stride;
-  cudaError_t e = launch_frame(inverse, i16, p->grid_frame, a, stream);
+  cudaError_t e = launch_frame(inverse, i16, inverse ? p->grid_frame : p->grid_frame_fwd, a, stream);
   if (e != cudaSuccess) return cuda_fail(e, "frame launch");
   return ADJ_OK;
 }
@@ -481,6 +482,7 @@ void apply_grid(adj_plan* p) {
   p->grid_inv = std::max(1, c > 0 ? std::min(c, p->occ_inv) : p->occ_inv) * p->n_sm;
   p->grid_multi = std::max(1, c > 0 ? std::min(c, p->occ_multi) : p->occ_multi) * p->n_sm;
   p->grid_frame = std::max(1, c > 0 ? std::min(c, p->occ_frame) : p->occ_frame) * p->n_sm;
+  p->grid_frame_fwd = std::max(1, c > 0 ? std::min(c, p->occ_frame_fwd) : p->occ_frame_fwd) * p->n_sm;
   p->grid_f32 = std::max(1, c > 0 ? std::min(c, p->occ_f32) : p->occ_f32) * p->n_sm;
 }
 
@@ -937,35 +939,40 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
   }
   for (int inv = 0; inv < 2 && !rc; ++inv) {
     const void* fn = fused_kernel_ptr(inv, p->threads);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    const int smem = fused_dyn_smem(inv, kModePacked);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, smem);
     if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
     else (inv ? p->occ_inv : p->occ_fwd) = std::max(1, occ);
   }
   if (!rc) {
     const void* fn = multi_kernel_ptr();
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    const int smem = fused_dyn_smem(false, kModeMulti);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, smem);
     if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
     else p->occ_multi = std::max(1, occ);
   }
   if (!rc) {
     const void* fn = fwd_f32_kernel_ptr();
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    const int smem = fused_dyn_smem(false, kModePackedF32);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, smem);
     if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
     else p->occ_f32 = std::max(1, occ);
   }
   for (int v = 0; v < 3 && !rc; ++v) {  // frame forward, inverse FP32, inverse int16
     const void* fn = frame_kernel_ptr(v > 0, v == 2);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    const int smem = fused_dyn_smem(v > 0, v == 2 ? kModeFrameI16 : kModeFrame);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, kSmemBytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p->threads, smem);
     if (e != cudaSuccess) rc = cuda_fail(e, "kernel attributes");
-    else p->occ_frame = v == 0 ? std::max(1, occ) : std::min(p->occ_frame, std::max(1, occ));
+    else if (v == 0) p->occ_frame_fwd = std::max(1, occ);
+    else p->occ_frame = v == 1 ? std::max(1, occ) : std::min(p->occ_frame, std::max(1, occ));
   }
   if (!rc) {
     for (int i = 0; i < 25; ++i) p->tuning.cap_div[i] = 1;

@@ -482,7 +482,7 @@ __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __r
   } else {
     src.template load<N>(v);
   }
-  if (!INV) {
+  if constexpr (!INV) {
     if (tf.kind == KIND_BAND) band<N, false>(v, tf, P);
     if (tf.kind != KIND_DENSE) core_apply<N>(tf.core, v);
     if (tf.kind >= KIND_POST) {

@@ -15,7 +15,7 @@ cudaError_t launch_frame(bool inverse, bool i16, int grid, const FusedArgs& args
   if (!inverse && i16) return cudaErrorInvalidValue;
   FusedArgs a = args;
   void* params[] = {&a};
-  return cudaLaunchKernel(frame_kernel_ptr(inverse, i16), dim3(grid), dim3(64), params, kSmemBytes, stream);
+  return cudaLaunchKernel(frame_kernel_ptr(inverse, i16), dim3(grid), dim3(64), params, fused_dyn_smem(inverse, inverse && i16 ? kModeFrameI16 : kModeFrame), stream);
 }
 
 }  // namespace adjtx

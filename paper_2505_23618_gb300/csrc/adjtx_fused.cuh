@@ -80,6 +80,115 @@ __device__ __forceinline__ void stage_tile_w(const TileDev& td, const uint32_t* 
   }
 }
 
+// int16 staging buffer of the forward (kernels with int16 input).  Line l of a tile (block
+// l / h, row l % h) holds its w samples at int16 offset l * w; 16-byte chunk q (8 samples) of
+// the line sits at chunk slot q ^ g(l), with g spreading 8 consecutive lines over 8 distinct
+// 16-byte bank groups (the FP32 swizzle of a line of w / 2 samples, taken on the line index so
+// that it also holds across blocks of 4 rows).  Lines of 4 samples (8 bytes) are dense.
+template <int W>
+__device__ __forceinline__ int s16_swz(int l) {
+  if constexpr (W >= 8) {
+    return (l >> sw_shift(W / 2)) & sw_mask(W / 2);
+  } else {
+    return 0;
+  }
+}
+
+template <int W, int THREADS>
+__device__ __forceinline__ void stage_i16_w(const TileDev& td, const uint32_t* sOff, const int16_t* src,
+                                            int16_t* S) {
+  const int h = td.h, nb = td.nblk, lgh = lg2(h);
+  if constexpr (W >= 8) {
+    constexpr int LG_CPR = ilog2(W / 8);
+    const int lg_cpb = LG_CPR + lgh, total = nb << lg_cpb;
+    for (int g = threadIdx.x; g < total; g += THREADS) {
+      const int b = g >> lg_cpb, gg = g & ((1 << lg_cpb) - 1);
+      const int l = (b << lgh) + (gg >> LG_CPR), q = gg & ((1 << LG_CPR) - 1);
+      cp_async16(S + l * W + ((q ^ s16_swz<W>(l)) << 3), src + (size_t)sOff[b] * 16 + gg * 8);
+    }
+  } else {
+    // 4-wide blocks are 8h contiguous bytes in both places: 16-byte copies of two rows each
+    const int lg_cpb = lgh - 1, total = nb << lg_cpb;
+    for (int g = threadIdx.x; g < total; g += THREADS) {
+      const int b = g >> lg_cpb, gg = g & ((1 << lg_cpb) - 1);
+      cp_async16(S + (b << (lgh + 2)) + gg * 8, src + (size_t)sOff[b] * 16 + gg * 8);
+    }
+  }
+}
+
+template <int W, int THREADS>
+__device__ __forceinline__ void stage_frame_i16_w(const TileDev& td, const uint32_t* sAux, const int16_t* frame,
+                                                  int64_t stride, int16_t* S) {
+  const int h = td.h, nb = td.nblk, lgh = lg2(h);
+  if constexpr (W == 4) {
+    const int total = nb << lgh;
+    for (int g = threadIdx.x; g < total; g += THREADS) {
+      const int b = g >> lgh, r = g & (h - 1);
+      cp_async8(S + g * 4, frame + (size_t)sAux[b] * 4 + (size_t)r * stride);
+    }
+  } else {
+    constexpr int LG_CPR = ilog2(W / 8);
+    const int lg_cpb = LG_CPR + lgh, total = nb << lg_cpb;
+    for (int g = threadIdx.x; g < total; g += THREADS) {
+      const int b = g >> lg_cpb, gg = g & ((1 << lg_cpb) - 1);
+      const int r = gg >> LG_CPR, q = gg & ((1 << LG_CPR) - 1), l = (b << lgh) + r;
+      const uint32_t a = sAux[b];
+      const int16_t* src = frame + (size_t)a * 4 + (size_t)r * stride + q * 8;
+      int16_t* dst = S + l * W + ((q ^ s16_swz<W>(l)) << 3);
+      if ((a & 1u) == 0) {
+        cp_async16(dst, src);
+      } else {
+        cp_async8(dst, src);
+        cp_async8(dst + 4, src + 4);
+      }
+    }
+  }
+}
+
+template <bool FRAME, int THREADS>
+__device__ __forceinline__ void stage_i16(const TileDev& td, const uint32_t* sIdx, const void* in, int64_t stride,
+                                          int16_t* S) {
+  const int16_t* src = static_cast<const int16_t*>(in);
+#define ADJ_STAGE16(W)                                         \
+  if constexpr (FRAME) {                                       \
+    stage_frame_i16_w<W, THREADS>(td, sIdx, src, stride, S);   \
+  } else {                                                     \
+    stage_i16_w<W, THREADS>(td, sIdx, src, S);                 \
+  }
+  switch (td.w) {
+    case 4: ADJ_STAGE16(4) break;
+    case 8: ADJ_STAGE16(8) break;
+    case 16: ADJ_STAGE16(16) break;
+    case 32: ADJ_STAGE16(32) break;
+    default: ADJ_STAGE16(64) break;
+  }
+#undef ADJ_STAGE16
+}
+
+// One line of the int16 staging buffer (see stage_i16_w).
+template <int W>
+struct RowS16 {
+  const int16_t* p;  // line start
+  int f;             // chunk swizzle of this line
+  template <int N>
+  __device__ __forceinline__ void load_i16(float (&v)[N]) const {
+    if constexpr (N == 4) {
+      const int2 r = *reinterpret_cast<const int2*>(p);
+      v[0] = (float)(int16_t)(r.x & 0xffff); v[1] = (float)(r.x >> 16);
+      v[2] = (float)(int16_t)(r.y & 0xffff); v[3] = (float)(r.y >> 16);
+    } else {
+#pragma unroll
+      for (int q = 0; q < N / 8; ++q) {
+        const int4 r = *reinterpret_cast<const int4*>(p + ((q ^ f) << 3));
+        v[8 * q + 0] = (float)(int16_t)(r.x & 0xffff); v[8 * q + 1] = (float)(r.x >> 16);
+        v[8 * q + 2] = (float)(int16_t)(r.y & 0xffff); v[8 * q + 3] = (float)(r.y >> 16);
+        v[8 * q + 4] = (float)(int16_t)(r.z & 0xffff); v[8 * q + 5] = (float)(r.z >> 16);
+        v[8 * q + 6] = (float)(int16_t)(r.w & 0xffff); v[8 * q + 7] = (float)(r.w >> 16);
+      }
+    }
+  }
+};
+
 // Forward from a frame: block b's row r starts at sample (aux_b * 4 + r * stride) of the int16
 // frame (stride a multiple of 8).  Each 8-sample chunk q of a row goes to its chunk slot
 // q ^ f(r) as one 16-byte copy when the block starts on an 8-sample boundary, else as two
@@ -157,6 +266,31 @@ __device__ __forceinline__ void row_pass(const TfDev& tf, const float* __restric
       const int r = l & (h - 1);
       RowSw row{buf + l * W, (r >> SH) & MK};
       line_transform<W, INV, I16>(tf, P, row, row);
+    }
+  }
+}
+
+// Forward row pass of kernels with int16 input: lines read from the int16 staging buffer S,
+// transformed, and written as FP32 rows into the tile buffer.
+template <int W, int THREADS>
+__device__ __forceinline__ void row_pass_s16(const TfDev& tf, const float* __restrict__ P, const int16_t* S,
+                                             float* buf, int nb, int h) {
+  constexpr int SH = sw_shift(W), MK = sw_mask(W);
+  const int nlines = nb * h;
+  if constexpr (W <= 32) {
+    const int half = nlines >> 1;  // nb * h is even (h >= 4)
+    for (int l = threadIdx.x; l < half; l += THREADS) {
+      const int l2 = l + half;
+      const Pair<RowS16<W>> src{RowS16<W>{S + l * W, s16_swz<W>(l)}, RowS16<W>{S + l2 * W, s16_swz<W>(l2)}};
+      const Pair<RowSw> dst{RowSw{buf + l * W, ((l & (h - 1)) >> SH) & MK},
+                            RowSw{buf + l2 * W, ((l2 & (h - 1)) >> SH) & MK}};
+      line_transform<W, false, true, float2>(tf, P, src, dst);
+    }
+  } else {
+    for (int l = threadIdx.x; l < nlines; l += THREADS) {
+      const RowS16<W> src{S + l * W, s16_swz<W>(l)};
+      const RowSw dst{buf + l * W, ((l & (h - 1)) >> SH) & MK};
+      line_transform<W, false, true>(tf, P, src, dst);
     }
   }
 }
@@ -390,9 +524,18 @@ __device__ __forceinline__ void multi_after_rows(const TfDev& th, const TfDev& t
 #undef ADJ_MULTI_W
 }
 
-// Shared memory limits residency to kSmemCtasPerSm CTAs per SM; the register budget
-// follows from that, so spills are never traded for occupancy that smem forbids.
-constexpr int kSmemCtasPerSm = (227 * 1024) / (kSmemBytes + 3072);
+// Resident CTAs per SM that shared memory allows for a kernel with dynamic shared memory
+// `dyn` and the static records of the fused kernel (aux: the per-block auxiliary lists of
+// the Multiple and frame modes); the register budget follows from it, so spills are never
+// traded for occupancy that shared memory forbids.
+constexpr int fused_static_smem(bool aux) {
+  return 3 * (kMaxTileBlocks + 4) * 4 + (aux ? 3 * (kMaxTileBlocks + 4) * 4 : 16) + 4 * 64 + 4 * 16 + 64;
+}
+constexpr int fused_ctas_per_sm(bool inverse, int mode) {
+  return kSmemPerSm / (fused_dyn_smem(inverse, mode) +
+                       fused_static_smem(mode == kModeMulti || mode == kModeFrame || mode == kModeFrameI16) +
+                       kSmemReservedPerCta);
+}
 
 // Copies a small record (a multiple of 16 bytes) from global to shared memory
 // asynchronously, spread over the CTA's threads.
@@ -403,12 +546,12 @@ __device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes
 }
 
 template <bool INV, int THREADS, int MODE = kModePacked>
-__global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / THREADS) fused_kernel(FusedArgs a) {
   constexpr bool MULTI = MODE == kModeMulti;
   constexpr bool FRAME_IN = !INV && MODE == kModeFrame;   // forward reading blocks from a frame
   constexpr int OUT = !INV || MODE < kModeFrame ? 0 : (MODE == kModeFrame ? 1 : 2);
   constexpr bool AUX = MODE == kModeMulti || MODE == kModeFrame || MODE == kModeFrameI16;
-  constexpr bool F32_IN = INV || MODE == kModePackedF32;  // staged input is FP32 (else int16)
+  constexpr bool F32_IN = !fused_i16_input(INV, MODE);  // staged input is FP32 (else int16)
   static_assert(!(INV && MULTI), "the Multiple form is forward only");
   static_assert(!(INV && MODE == kModePackedF32), "FP32 input is the inverse's own");
   static_assert(INV || MODE != kModeFrameI16, "int16 output is for the inverse");
@@ -418,17 +561,31 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
   //   sOff[k % 3]    block offsets / 16 (k, k+1 valid; k+2 arrives); a tile's list starts at
   //                  entry blk_begin & 3 (it is copied from the 16-byte aligned address below)
   //   sTf[k % 2]     (horizontal, vertical) transform records (k valid; k+1 arrives)
-  //   sAux[k % 2]    Multiple / frame modes: side or frame offsets / 4, indexed like sOff
+  //   sAux[k % 3]    Multiple / frame modes: side or frame offsets / 4, indexed like sOff
   //                  (k valid; k+1 arrives; the frame forward also needs k+1 for staging)
-  // and tile k's data in buffer k % 2 while tile k+1 is being copied into the other one.
+  // Tile data: FP32 input is staged in place, tile k in buffer k % 2 while tile k+1 is copied
+  // into the other one.  int16 input has one tile buffer and one int16 staging buffer S: the
+  // row pass of tile k reads S and writes the buffer, then tile k+1 is copied into S while the
+  // column pass of tile k runs.
   __shared__ __align__(16) uint32_t sOff[3][kMaxTileBlocks + 4];
   __shared__ __align__(16) uint32_t sAux[AUX ? 3 : 1][AUX ? kMaxTileBlocks + 4 : 4];
   __shared__ __align__(16) TfDev sTf[2][2];
   __shared__ __align__(16) TileDev sDesc[4];
   __shared__ int sIdx[3];
+  int16_t* const S = reinterpret_cast<int16_t*>(smem + kBufBytes);  // int16 input only
   const int tid = threadIdx.x;
   Claimer cl;  // used by warp 0 only
   auto list_bytes = [](const TileDev& d) { return (((d.blk_begin & 3) + d.nblk + 3) / 4) * 16; };
+  // issue the copies of one tile's input: into buffer `buf` (FP32) or S (int16)
+  auto stage = [&](const TileDev& d, int slot, float* buf) {
+    if constexpr (F32_IN) {
+      stage_tile<true, THREADS>(d, sOff[slot] + (d.blk_begin & 3), a.in, buf);
+    } else if constexpr (FRAME_IN) {
+      stage_i16<true, THREADS>(d, sAux[slot] + (d.blk_begin & 3), a.in, a.frame_stride, S);
+    } else {
+      stage_i16<false, THREADS>(d, sOff[slot] + (d.blk_begin & 3), a.in, 0, S);
+    }
+  };
 
   // Prologue: warp 0 claims three tiles and puts a claim for a fourth in flight; fetch the records
   // of tile 0, stage it, and start fetching the offsets of tile 1 and the descriptor of tile 2.
@@ -457,11 +614,7 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
       for (int b = tid; b < d0.nblk; b += THREADS) sAux[0][(d0.blk_begin & 3) + b] = a.tile_aux[d0.blk_begin + b];
     }
     __syncthreads();
-    if constexpr (FRAME_IN) {
-      stage_frame<THREADS>(d0, sAux[0] + (d0.blk_begin & 3), a.in, a.frame_stride, reinterpret_cast<float*>(smem));
-    } else {
-      stage_tile<F32_IN, THREADS>(d0, sOff[0] + (d0.blk_begin & 3), a.in, reinterpret_cast<float*>(smem));
-    }
+    stage(d0, 0, reinterpret_cast<float*>(smem));
     if (tn >= 0) {
       const TileDev d1 = a.tiles[tn];
       if (tid == 0) sDesc[1] = d1;
@@ -473,12 +626,12 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
   }
 
   // Per tile k: (1) wait for everything fetched during the previous iteration, barrier;
-  // (2) start copying tile k+1 into the other buffer, with its records, and the offsets of
-  // tile k+2; warp 0 reads the claim issued an iteration ago (tile k+3), fetches that
-  // tile's descriptor and issues the claim of tile k+4; (3) row pass; (4) barrier;
-  // (5) column pass.  The copies of tile k+1 overlap both passes of tile k.
+  // (2) FP32 input: start copying tile k+1 into the other buffer; both: fetch the transform
+  // records of tile k+1 and the offsets of tile k+2; warp 0 reads the claim issued an
+  // iteration ago (tile k+3), fetches that tile's descriptor and issues the claim of tile k+4;
+  // (3) row pass; (4) barrier; int16 input: start copying tile k+1 into S; (5) column pass.
   for (int k = 0; t >= 0; ++k) {
-    const int cur = k & 1;
+    const int cur = F32_IN ? (k & 1) : 0;
     float* buf = reinterpret_cast<float*>(smem + cur * kBufBytes);
     // (1)
     cp_async_wait_all();
@@ -487,14 +640,9 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
     // (2)
     if (tn >= 0) {
       const TileDev dn = sDesc[(k + 1) & 3];
-      float* nbuf = reinterpret_cast<float*>(smem + (cur ^ 1) * kBufBytes);
-      if constexpr (FRAME_IN) {
-        stage_frame<THREADS>(dn, sAux[(k + 1) % 3] + (dn.blk_begin & 3), a.in, a.frame_stride, nbuf);
-      } else {
-        stage_tile<F32_IN, THREADS>(dn, sOff[(k + 1) % 3] + (dn.blk_begin & 3), a.in, nbuf);
-      }
-      copy_async<THREADS>(&sTf[cur ^ 1][0], a.tfs + dn.tf_h, sizeof(TfDev));
-      copy_async<THREADS>(&sTf[cur ^ 1][1], a.tfs + dn.tf_v, sizeof(TfDev));
+      if constexpr (F32_IN) stage(dn, (k + 1) % 3, reinterpret_cast<float*>(smem + (cur ^ 1) * kBufBytes));
+      copy_async<THREADS>(&sTf[(k + 1) & 1][0], a.tfs + dn.tf_h, sizeof(TfDev));
+      copy_async<THREADS>(&sTf[(k + 1) & 1][1], a.tfs + dn.tf_v, sizeof(TfDev));
     }
     if (tn2 >= 0) {
       const TileDev dn2 = sDesc[(k + 2) & 3];
@@ -512,27 +660,43 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
     }
     cp_async_commit();
 
-    // (3) row pass (horizontal transform, length w), in place
+    // (3) row pass (horizontal transform, length w): in place (FP32 input) or S -> buffer
     const int w = td.w, h = td.h, nb = td.nblk;
     {
-      TfDev tf = sTf[cur][0];
+      TfDev tf = sTf[k & 1][0];
       if constexpr (MULTI) tf.kind = KIND_NONE;  // the rows get the plain DCT-2 first
-      switch (w) {
-        case 4: row_pass<4, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
-        case 8: row_pass<8, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
-        case 16: row_pass<16, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
-        case 32: row_pass<32, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
-        default: row_pass<64, INV, THREADS, !F32_IN>(tf, a.params, buf, nb, h); break;
+      if constexpr (F32_IN) {
+        switch (w) {
+          case 4: row_pass<4, INV, THREADS, false>(tf, a.params, buf, nb, h); break;
+          case 8: row_pass<8, INV, THREADS, false>(tf, a.params, buf, nb, h); break;
+          case 16: row_pass<16, INV, THREADS, false>(tf, a.params, buf, nb, h); break;
+          case 32: row_pass<32, INV, THREADS, false>(tf, a.params, buf, nb, h); break;
+          default: row_pass<64, INV, THREADS, false>(tf, a.params, buf, nb, h); break;
+        }
+      } else {
+        switch (w) {
+          case 4: row_pass_s16<4, THREADS>(tf, a.params, S, buf, nb, h); break;
+          case 8: row_pass_s16<8, THREADS>(tf, a.params, S, buf, nb, h); break;
+          case 16: row_pass_s16<16, THREADS>(tf, a.params, S, buf, nb, h); break;
+          case 32: row_pass_s16<32, THREADS>(tf, a.params, S, buf, nb, h); break;
+          default: row_pass_s16<64, THREADS>(tf, a.params, S, buf, nb, h); break;
+        }
       }
     }
     // (4)
     __syncthreads();
     const int tn3 = sIdx[0];
+    if constexpr (!F32_IN) {
+      if (tn >= 0) {
+        stage(sDesc[(k + 1) & 3], (k + 1) % 3, nullptr);
+        cp_async_commit();
+      }
+    }
     // (5) column pass (vertical transform, length h), stores to global memory
     const uint32_t* offs = sOff[k % 3] + (td.blk_begin & 3);
     if constexpr (MULTI) {
       const uint32_t* sides = sAux[k % 3] + (td.blk_begin & 3);
-      const TfDev th = sTf[cur][0], tv = sTf[cur][1];
+      const TfDev th = sTf[k & 1][0], tv = sTf[k & 1][1];
       switch (h) {
         case 4: multi_after_rows<4, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
         case 8: multi_after_rows<8, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
@@ -541,7 +705,7 @@ __global__ void __launch_bounds__(THREADS, kSmemCtasPerSm * 64 / THREADS) fused_
         default: multi_after_rows<64, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
       }
     } else {
-      const TfDev tf = sTf[cur][1];
+      const TfDev tf = sTf[k & 1][1];
       const uint32_t* aux = sAux[AUX ? k % 3 : 0] + (td.blk_begin & 3);
       const int st = (int)a.frame_stride;
       switch (h) {

@@ -15,7 +15,7 @@ cudaError_t launch_fused(bool inverse, int threads, int grid, const FusedArgs& a
   if (!fn) return cudaErrorInvalidValue;
   FusedArgs a = args;
   void* params[] = {&a};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, kSmemBytes, stream);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, fused_dyn_smem(inverse, kModePacked), stream);
 }
 
 }  // namespace adjtx

@@ -9,7 +9,7 @@ const void* fwd_f32_kernel_ptr() { return reinterpret_cast<const void*>(&fused_k
 cudaError_t launch_fwd_f32(int grid, const FusedArgs& args, cudaStream_t stream) {
   FusedArgs a = args;
   void* params[] = {&a};
-  return cudaLaunchKernel(fwd_f32_kernel_ptr(), dim3(grid), dim3(64), params, kSmemBytes, stream);
+  return cudaLaunchKernel(fwd_f32_kernel_ptr(), dim3(grid), dim3(64), params, fused_dyn_smem(false, kModePackedF32), stream);
 }
 
 }  // namespace adjtx

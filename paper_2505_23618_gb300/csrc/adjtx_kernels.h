@@ -29,6 +29,14 @@ struct FusedArgs {
 // Kernel modes (template argument of the fused kernel).
 enum { kModePacked = 0, kModeMulti = 1, kModeFrame = 2, kModeFrameI16 = 3, kModePackedF32 = 4 };
 
+// Dynamic shared memory of a fused-kernel instantiation: int16 input (forward from packed
+// blocks, frames, and the Multiple forward) has its own staging buffer beside one FP32 tile
+// buffer; FP32 input is staged in place into two tile buffers.
+ADJ_HD bool fused_i16_input(bool inverse, int mode) { return !inverse && mode != kModePackedF32; }
+ADJ_HD int fused_dyn_smem(bool inverse, int mode) {
+  return fused_i16_input(inverse, mode) ? kSmemBytesI16 : kSmemBytes;
+}
+
 // Plain (unfused) form: the blocks of one size class, each with its own transforms.
 struct PlainBlock {
   uint32_t off16;

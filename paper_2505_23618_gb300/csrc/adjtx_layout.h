@@ -48,6 +48,14 @@ constexpr int kTileCoefs = 4096;
 constexpr int kBufBytes = 4 * kTileCoefs;
 constexpr int kSmemBytes = 2 * kBufBytes;
 constexpr int kMaxTileBlocks = 256;
+// Kernels whose input is int16 (the forward from residual blocks or frames) stage it into a
+// separate int16 buffer and write the row pass's FP32 output into one tile buffer: 24 KB
+// instead of 32 KB, which lets 8 CTAs share an SM.
+constexpr int kStageI16Bytes = 2 * kTileCoefs;
+constexpr int kSmemBytesI16 = kBufBytes + kStageI16Bytes;
+// Shared memory of one GB300 SM, and what the hardware reserves for each resident CTA.
+constexpr int kSmemPerSm = 228 * 1024;
+constexpr int kSmemReservedPerCta = 1024;
 
 // Work distribution.  The tile list is sorted by class, so consecutive tiles share
 // (w, h, core, adjustment) and therefore code.  The planner cuts the list into up to

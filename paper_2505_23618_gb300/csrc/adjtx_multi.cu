@@ -8,7 +8,7 @@ const void* multi_kernel_ptr() { return reinterpret_cast<const void*>(&fused_ker
 cudaError_t launch_multi(int grid, const FusedArgs& args, cudaStream_t stream) {
   FusedArgs a = args;
   void* params[] = {&a};
-  return cudaLaunchKernel(multi_kernel_ptr(), dim3(grid), dim3(64), params, kSmemBytes, stream);
+  return cudaLaunchKernel(multi_kernel_ptr(), dim3(grid), dim3(64), params, fused_dyn_smem(false, kModeMulti), stream);
 }
 
 }  // namespace adjtx

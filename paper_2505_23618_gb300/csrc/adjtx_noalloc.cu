@@ -16,6 +16,13 @@
 // share the array and it keeps the previous call's contents; each call clears the work
 // scheduling state and rewrites everything else it reads.  Calls that overlap on the GPU (two
 // streams, or two host threads) race on the array and must be serialised by the caller.
+//
+// The records and parameters are uploaded from host memory that lives only for the call (the
+// caller's stack and a per-thread array reused by the next call).  A copy recorded into a
+// CUDA graph would read that memory again at every replay, long after it is gone, so a call
+// made while its stream is capturing is rejected before anything is enqueued.  Because the
+// uploads come from pageable memory, the call may also block the host until the work already
+// queued on the stream has finished.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -82,8 +89,9 @@ int setup(int dev, unsigned char** ptr, int* grid) {
     int n_sm = 0, occ = 0;
     const void* fn = fused_kernel_ptr(false, kThreads);
     e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, kSmemBytes);
+    const int smem = fused_dyn_smem(false, kModePacked);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
     if (e != cudaSuccess) return cuda_err(e, "no-alloc set-up");
     g_grid[dev] = (occ > 0 ? occ : 1) * n_sm;
     g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
@@ -211,6 +219,13 @@ extern "C" int adj_transform_fwd_uniform_noalloc(const adj_1d_desc_t* tf_h, cons
   if (!d_resid || !d_coef) return err(ADJ_ERR_INVALID_ARG, "null device buffer");
   if (reinterpret_cast<uintptr_t>(d_resid) % 16 || reinterpret_cast<uintptr_t>(d_coef) % 16)
     return err(ADJ_ERR_MISALIGNED, "device buffers must be 16-byte aligned");
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(stream, &capture);
+  if (ce != cudaSuccess) return cuda_err(ce, "cudaStreamIsCapturing");
+  if (capture != cudaStreamCaptureStatusNone)
+    return err(ADJ_ERR_INVALID_ARG,
+               "adj_transform_fwd_uniform_noalloc cannot be recorded into a CUDA graph: its uploads read "
+               "host memory that lives only for the call");
 
   TfDev recs[2];
   // per-thread host staging of the parameters (a static array: no allocation per call)
