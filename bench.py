@@ -52,6 +52,7 @@ def parse():
                    help="measure the large-frame workload (default)")
     p.add_argument("--no-uhd8k", dest="uhd8k", action="store_false")
     p.add_argument("--no-frame", action="store_true", help="skip the frame-layout measurement")
+    p.add_argument("--no-bwd", action="store_true", help="skip the backward / fitter-step measurement")
     p.add_argument("--classes", action="store_true",
                    help="diagnostic: time uniform single-class workloads (one JSON line per class) instead")
     return p.parse_args()
@@ -212,23 +213,86 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+_ORACLE_JOBS = None
+
+
+def _oracle_init(jobs):
+    global _ORACLE_JOBS
+    _ORACLE_JOBS = jobs
+
+
+def _oracle_chunk_roundtrip(i):
+    """One worker's share of the CPU baseline: FP64 oracle forward then inverse of a
+    contiguous run of blocks (data rebased to the run's first sample), handed to the workers
+    once when the pool starts."""
+    import oracle
+    data, blocks, tfs = _ORACLE_JOBS[i]
+    oracle.inverse_blocks(oracle.forward_blocks(data, blocks, tfs), blocks, tfs)
+    return int(data.size)
+
+
+def oracle_chunks(data, blocks, tfs, n_chunks):
+    """Cut a packed block list (offsets increasing, blocks back to back) into about n_chunks
+    contiguous runs of similar coefficient counts, each with its own data slice."""
+    import numpy as np
+    sz = blocks["w"].astype(np.int64) * blocks["h"]
+    cs = np.cumsum(sz)
+    cuts = np.searchsorted(cs, np.linspace(0, cs[-1], n_chunks + 1)[1:-1])
+    jobs = []
+    for part in np.split(np.arange(blocks.size), cuts):
+        if part.size == 0:
+            continue
+        b = blocks[part].copy()
+        lo = int(b["offset"][0])
+        hi = int(b["offset"][-1] + sz[part[-1]])
+        b["offset"] -= lo
+        jobs.append((np.ascontiguousarray(data[lo:hi]), b, tfs))
+    return jobs
+
+
+def oracle_pool(cores, jobs):
+    """Process pool for the oracle, one single-threaded worker per core (BLAS pinned to one
+    thread per process), each holding the jobs; started with spawn so that no worker inherits
+    GPU state."""
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    return mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(jobs,))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(sample_desc="full workload (66.4 M coefficients), one forward + one inverse"):
-    """Time the FP64 oracle on the host (single process, BLAS pinned to 1 thread)."""
+    """Time the FP64 oracle on the host cores: a process pool (one single-threaded worker
+    per core) over contiguous runs of blocks, in a child process started before any GPU work
+    of its own."""
+    cores = host_cores()
     code = (
         "import time, json, sys; sys.path.insert(0, %r)\n"
-        "import numpy as np, synth, oracle\n"
-        "wl = synth.uhd_mixed()\n"
-        "t = time.perf_counter(); y = oracle.forward_blocks(wl.data, wl.blocks, wl.tfs)\n"
-        "x = oracle.inverse_blocks(y, wl.blocks, wl.tfs); dt = time.perf_counter() - t\n"
-        "print(json.dumps({'coefs': int(wl.total), 'seconds': dt}))\n" % ROOT)
+        "import bench, synth\n"
+        "if __name__ == '__main__':\n"
+        "    wl = synth.uhd_mixed()\n"
+        "    jobs = bench.oracle_chunks(wl.data, wl.blocks, wl.tfs, 4 * %d)\n"
+        "    with bench.oracle_pool(%d, jobs) as pool:\n"
+        "        pool.map(bench._oracle_chunk_roundtrip, range(%d), chunksize=1)\n"
+        "        t = time.perf_counter()\n"
+        "        n = sum(pool.map(bench._oracle_chunk_roundtrip, range(len(jobs)), chunksize=1))\n"
+        "        dt = time.perf_counter() - t\n"
+        "    print(json.dumps({'coefs': int(n), 'seconds': dt}))\n" % (ROOT, cores, cores, cores))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc,
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc,
                 "error": r.stderr[-300:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["coefs"] / d["seconds"] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample_desc, "seconds": round(d["seconds"], 3)}
+    return {"value": d["coefs"] / d["seconds"] / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample_desc + f", {cores} single-threaded processes over contiguous block runs",
+            "seconds": round(d["seconds"], 3)}
 
 
 def run_reference(args):
@@ -236,29 +300,33 @@ def run_reference(args):
     if rank != 0:
         return 0
     import numpy as np
-    import oracle
     import synth
     wl = workload(0)
-    # each step transforms a bounded sample of the workload: the first ~1 M coefficients
+    cores = host_cores()
+    # each step transforms a bounded sample of the workload: its first ~1 M coefficients per
+    # host core, split over the cores in contiguous runs of blocks
     cs = np.cumsum(wl.blocks["w"].astype(np.int64) * wl.blocks["h"])
-    nb = int(np.searchsorted(cs, 1_000_000)) + 1
+    nb = int(np.searchsorted(cs, 1_000_000 * cores)) + 1
+    nb = min(nb, int(wl.blocks.size))
     blocks, tot = wl.blocks[:nb], int(cs[nb - 1])
-    data = wl.data[:tot]
-    for _ in range(args.warmup):
-        oracle.inverse_blocks(oracle.forward_blocks(data, blocks, wl.tfs), blocks, wl.tfs)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.inverse_blocks(oracle.forward_blocks(data, blocks, wl.tfs), blocks, wl.tfs)
-    dt = time.perf_counter() - t0
+    jobs = oracle_chunks(wl.data[:tot], blocks, wl.tfs, 4 * cores)
+    with oracle_pool(cores, jobs) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_chunk_roundtrip, range(len(jobs)), chunksize=1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_chunk_roundtrip, range(len(jobs)), chunksize=1)
+        dt = time.perf_counter() - t0
     value = tot * args.steps / dt / 1e9
-    sample = f"first {nb} blocks ({tot} coefficients) of the workload per step"
+    sample = (f"first {nb} blocks ({tot} coefficients) of the workload per step, "
+              f"{cores} single-threaded processes over contiguous block runs")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl.name, "coefs": tot, "blocks": nb, "what": "FP64 CPU oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -418,6 +486,60 @@ def bench_uhd8k(args, rank, dev, stream, flush, peak):
     return out
 
 
+def bench_bwd(args, rank, dev, stream, flush, peak):
+    """Backward of the two DST-7 fits at their full size (65,536 AR(1) 64x64 blocks, one 1-D
+    transform used in both directions): the 64-point DCT-2 with the 24-tap band (378 angles)
+    and the 64-point DST-2 with the 32x32 Cayley post block.  Times adj_transform_bwd alone
+    (dL/dparams from x and dL/dY, the fitter's call; CUDA events, median of L2-flushed
+    repeats) and one whole fitter step (forward, coding-gain proxy, backward, host Adam;
+    wall clock).  Algorithmic bytes: x (int16) and dL/dY (FP32), 6 per coefficient; flops:
+    the outer products sum a b^T (2 m^2 per line and direction, m = 64 for the band, 32 for
+    the post block) plus three line transforms per line and direction (the recomputed
+    forward, the transposed pass of dL/dY and the recomputed input of the row gradients)."""
+    import numpy as np
+    import torch
+    from paper_2505_23618_gb300.fit import FitConfig, Fitter
+
+    reps = max(3, min(args.steps, 10))
+    out = {"workload": "65536 blocks 64x64 AR(1) rho 0.95 sigma 40 (the fits' blocks)", "unit": UNIT}
+    for name, cfg in (("band_dct2_378", FitConfig(core=0, kind=1, seed=4 + 1000 * rank)),
+                      ("post_dst2_k32", FitConfig(core=2, kind=2, seed=4 + 1000 * rank))):
+        f = Fitter(cfg, device=dev)
+        coefs = int(f.x.numel())
+        f.loss_and_grad()
+        gy = torch.randn(coefs, device=dev)
+        for _ in range(2):
+            f.plan.bwd(f.x, gy, None, f.gp, stream)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps)]
+        for e in ev:
+            flush.fill_(3.0)
+            e[0].record(stream)
+            f.plan.bwd(f.x, gy, None, f.gp, stream)
+            e[1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        t0 = time.perf_counter()
+        steps = 3
+        for _ in range(steps):
+            f.step()
+        step_ms = (time.perf_counter() - t0) / steps * 1e3
+        lines = 2 * 64 * (coefs // 4096)
+        m = 64 if cfg.kind == 1 else cfg.k
+        import synth
+        lf = line_flops(synth.Tf(n=64, core=cfg.core, kind=cfg.kind, angles=np.asarray(f.theta))
+                        if cfg.kind == 1 else synth.Tf(n=64, core=cfg.core, kind=cfg.kind, q=f.q()))
+        flops = lines * (2 * m * m + 3 * lf)
+        gbs = coefs * 6 / (ms * 1e-3) / 1e9
+        out[name] = {"bwd_ms": round(ms, 4), "GB/s": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
+                     "flops_per_coef": round(flops / coefs, 1),
+                     "alu": alu_roofline(flops, ms), "fit_step_ms": round(step_ms, 2),
+                     "coef_per_s_bwd": round(coefs / (ms * 1e-3) / 1e9, 3)}
+        f.plan.close()
+        del f, gy
+    out["how"] = f"median of {reps} L2-flushed repeats; fit step: wall clock of 3 steps"
+    return out
+
+
 def bench_frame(args, rank, dev, stream, flush, peak):
     """Blocks inside frames (no packing step): forward from an int16 residual frame and inverse
     back into an int16 frame (rounded), on 8 frames of 3840x2160 tiled like the mixed UHD
@@ -565,6 +687,7 @@ def run_fused(args):
     multiple = bench_multiple(args, rank, dev, stream, flush, peak) if not args.no_multiple else None
     uhd8k = bench_uhd8k(args, rank, dev, stream, flush, peak) if args.uhd8k else None
     frame = bench_frame(args, rank, dev, stream, flush, peak) if not args.no_frame else None
+    bwd = bench_bwd(args, rank, dev, stream, flush, peak) if not args.no_bwd else None
 
     # end to end through the host-buffer C-ABI calls (pinned memory), copies included
     h_x = torch.from_numpy(wl.data).pin_memory()
@@ -623,6 +746,7 @@ def run_fused(args):
             "multiple": multiple,
             "uhd8k": uhd8k,
             "frame": frame,
+            "bwd": bwd,
             "kernels": {k: {"ms": round(v["ms"], 4), "GB/s": round(v["gbs"], 1), "frac": round(v["frac"], 4)}
                         for k, v in kern.items()},
             "flops_per_coef": round(flops / coefs, 2),

@@ -398,16 +398,55 @@ def run_fit(name, steps, lr=0.01, log_every=0):
     return rec
 
 
+def basis_table(rec):
+    """Basis vector by basis vector comparison of a stored band fit with the DST-7 it
+    approximates (the content of Fig. 3, in numbers): for every row k of the fitted transform
+    H = B A, the distance |h_k - d_k|, the inner product <h_k, d_k>, the distance of the core
+    B alone, and the weight e^{-alpha k} (alpha = ln(100)/N) that Eq. 2 gives the row.  Host
+    FP64 only."""
+    n, core = int(rec["config"]["n"]), int(rec["config"]["core"])
+    H = band_H(n, core, tuple(rec["parities"]), np.asarray(rec["angles"], dtype=np.float64))
+    D = targets.dst7(n)
+    B = targets.core(n, core)
+    alpha = math.log(100.0) / n
+    rows = []
+    for k in range(n):
+        rows.append({"k": k, "dist": float(np.linalg.norm(H[k] - D[k])), "inner": float(H[k] @ D[k]),
+                     "core_dist": float(np.linalg.norm(B[k] - D[k])), "weight": math.exp(-alpha * k)})
+    return rows
+
+
+def basis_table_markdown(rec):
+    rows = basis_table(rec)
+    out = ["| k | Eq. 2 weight | core alone: |b_k - d_k| | fitted: |h_k - d_k| | <h_k, d_k> |",
+           "|---|---|---|---|---|"]
+    for r in rows:
+        out.append(f"| {r['k']} | {r['weight']:.3f} | {r['core_dist']:.4f} | {r['dist']:.4f} | {r['inner']:.4f} |")
+    return "\n".join(out)
+
+
 def main(argv=None):
     import argparse
     import time
     ap = argparse.ArgumentParser(description="Fit the DST-7 adjustments on the GPU and write them as JSON.")
-    ap.add_argument("--out", required=True, help="output JSON file")
+    ap.add_argument("--basis-table", metavar="FIT", default=None,
+                    help="print the basis-vector table of a stored band fit (host only; e.g. "
+                         "eq2_band6_dst3_16 from params/fitted_eq2.json) instead of fitting")
+    ap.add_argument("--params", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "params",
+                                                     "fitted_eq2.json"),
+                    help="stored fits for --basis-table")
+    ap.add_argument("--out", help="output JSON file (fitting)")
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--lr", type=float, default=0.01)
     ap.add_argument("--only", nargs="*", default=None,
                     help="names of the fits to run (default: the five design fits; see FITS)")
     a = ap.parse_args(argv)
+    if a.basis_table:
+        with open(a.params) as fh:
+            print(basis_table_markdown(json.load(fh)[a.basis_table]))
+        return 0
+    if not a.out:
+        ap.error("--out is required when fitting")
     out = {}
     for name in (a.only or list(DESIGN_FITS)):
         t0 = time.time()

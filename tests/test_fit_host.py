@@ -74,3 +74,30 @@ def test_basis_and_eq2_terms():
     assert math.isclose(val, O.eq2_weighted_error(H, s.D), rel_tol=1e-12)
     wts = np.exp(-math.log(100.0) / n * np.arange(n))[:, None]
     assert np.allclose(dH, 2 * wts * (H - s.D))
+
+
+def test_basis_table_of_the_eq2_band_fit():
+    """The basis-vector table (Fig. 3 in numbers) of the stored 16-point Eq. 2 fit (6-tap band
+    before the DST-3): the fitted H is the oracle's adjusted matrix, every row is a unit vector
+    (|h - d|^2 = 2 - 2 <h, d>), and the low-frequency rows the criterion weights most are far
+    closer to the DST-7 than the high-frequency ones and than the core alone."""
+    import json
+    import os
+    import numpy as np
+    import oracle
+    from paper_2505_23618_gb300 import fit
+    path = os.path.join(os.path.dirname(fit.__file__), "params", "fitted_eq2.json")
+    with open(path) as f:
+        rec = json.load(f)["eq2_band6_dst3_16"]
+    H = fit.band_H(16, 3, tuple(rec["parities"]), np.asarray(rec["angles"]))
+    Ho = oracle.adjusted_matrix(16, 3, 1, rec["parities"], rec["angles"])
+    assert np.abs(H - Ho).max() <= 1e-12
+    rows = fit.basis_table(rec)
+    assert [r["k"] for r in rows] == list(range(16))
+    for r in rows:
+        assert abs(r["dist"] ** 2 - (2 - 2 * r["inner"])) <= 1e-12
+    low = [r["dist"] for r in rows[:8]]
+    high = [r["dist"] for r in rows[10:]]
+    assert max(low) < 0.06 < 0.15 < min(high)
+    assert all(r["dist"] < r["core_dist"] for r in rows)
+    assert "| 0 | 1.000 |" in fit.basis_table_markdown(rec)

@@ -350,3 +350,34 @@ def test_uhd_mixed_full_size_sampled():
 
 def test_uhd8k_full_size_sampled():
     assert _full_size(synth.uhd8k(), 1500, 5) <= REL_TOL
+
+
+def _fitted_uhd8k_tfs():
+    """The large-frame workload's transforms with the fitted parameters the benchmark times:
+    horizontal DST-3 + 12-layer band (Section 2.2), vertical DCT-2 + post block with the
+    DCT-8 block S Q S of Eq. 5 (K = 32 at 64 points, 16 at 32)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2505_23618_gb300", "params", "fitted.json")
+    with open(path) as f:
+        fit = json.load(f)
+    b = fit["band_dst3_64"]
+    h_tf = synth.Tf(n=64, core=synth.CORE_DST3, kind=synth.KIND_BAND,
+                    parities=np.array(b["parities"], np.uint8), angles=np.array(b["angles"]))
+    v_tfs = {}
+    for n in (64, 32):
+        p = fit[f"post_dct2_{n}"]
+        q7, q8 = np.array(p["q"]), np.array(p["q_dct8"])
+        # the stored DCT-8 block is the DST-7 one conjugated by the alternating signs (Eq. 5)
+        assert np.abs(q8 - oracle.post_c8_from_s7(q7)).max() <= 1e-12
+        v_tfs[n] = synth.Tf(n=n, core=synth.CORE_DCT2, kind=synth.KIND_POST, q=q8)
+    return h_tf, v_tfs
+
+
+def test_uhd8k_fitted_parameters_full_size_sampled():
+    """The 16-frame 8K workload with the fitted parameters of the benchmark: round trip and
+    per-block energy on every block, 1500 sampled blocks against the oracle."""
+    h_tf, v_tfs = _fitted_uhd8k_tfs()
+    assert h_tf.angles.size == 378
+    assert _full_size(synth.uhd8k(h_tf=h_tf, v_tfs=v_tfs), 1500, 55) <= REL_TOL
