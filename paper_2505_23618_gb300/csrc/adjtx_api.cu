@@ -227,23 +227,6 @@ void materialise(const std::vector<TfHost>& tfs, std::vector<float>* params, std
           params->push_back((float)v);
         }
     }
-    // duplicated tables for lines processed in packed pairs (n <= 32)
-    if (t.n <= 32 && t.kind == ADJ_ADJ_PRE_BAND) {
-      while (params->size() % 4) params->push_back(0.f);
-      d.cs2_off = (uint32_t)(params->size() / 4);
-      for (double a : t.angles) {
-        const float c = (float)std::cos(a), s = (float)std::sin(a);
-        params->insert(params->end(), {c, c, s, s});
-      }
-    } else if (t.n <= 32 && (t.kind == ADJ_ADJ_POST_BLOCK || t.kind == ADJ_ADJ_DENSE)) {
-      while (params->size() % 4) params->push_back(0.f);
-      d.q2_off = (uint32_t)params->size();
-      for (int i = 0; i < t.kt; ++i)
-        for (int j = 0; j < t.kt; ++j) {
-          const float v = (float)((i < t.k && j < t.k) ? t.q[i * t.k + j] : (i == j ? 1.0 : 0.0));
-          params->insert(params->end(), {v, v});
-        }
-    }
     devs->push_back(d);
   }
   while (params->size() % 4) params->push_back(0.f);

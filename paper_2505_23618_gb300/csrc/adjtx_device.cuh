@@ -13,9 +13,9 @@ namespace adjtx {
 // ---------------------------------------------------------------------------------
 // Element types.  T = float: one line per thread.  T = float2: two lines per thread,
 // element j of line 0 in .x and of line 1 in .y, processed by the packed FP32x2
-// instructions (one instruction per operation for both lines).  Runtime coefficients of a
-// packed line pair come from duplicated tables ({c, c, s, s} per rotation, {q, q} per Q
-// entry) so that they load as ready-made pairs.
+// instructions (one instruction per operation for both lines).  Runtime coefficients (cos,
+// sin of a rotation, entries of Q) are shared by both lines: they are loaded once as scalars
+// and broadcast to both halves of the FP32x2 operand, which costs no extra instruction.
 // ---------------------------------------------------------------------------------
 // log2 of a power of two at run time (one instruction instead of a loop).
 __device__ __forceinline__ int lg2(int x) { return 31 - __clz(x); }
@@ -48,9 +48,9 @@ __device__ __forceinline__ void load_cs(const float* P, const TfDev& tf, int idx
   s = t.y;
 }
 __device__ __forceinline__ void load_cs(const float* P, const TfDev& tf, int idx, float2& c, float2& s) {
-  const float4 t = __ldg(reinterpret_cast<const float4*>(P) + tf.cs2_off + idx);
-  c = make_float2(t.x, t.y);
-  s = make_float2(t.z, t.w);
+  const float2 t = __ldg(reinterpret_cast<const float2*>(P) + tf.cs_off + idx);
+  c = make_float2(t.x, t.x);
+  s = make_float2(t.y, t.y);
 }
 
 // Negation written per component, so that it folds into the FP32x2 FMA consuming it (one
@@ -113,8 +113,7 @@ __device__ __forceinline__ void band(T (&v)[N], const TfDev& tf, const float* __
 // major) acts on the first KT outputs.  Forward: y_i = sum_j Qp[i][j] u_j, written out
 // directly at runtime index i (several rows per step, independent accumulators).
 // Inverse (C^T): u_j = sum_i Qp[i][j] y_i with y_i read back from the source line.
-// Four consecutive entries of a Q row load as one float4 (scalar lines) or two {q, q}
-// pairs (packed lines).
+// Four consecutive entries of a Q row load as one float4.
 // ---------------------------------------------------------------------------------
 // Rows of Qp handled per step: enough independent accumulators for ILP while the Q
 // loads the compiler hoists out of the unrolled dot product still fit in registers.
@@ -128,27 +127,20 @@ __device__ __forceinline__ void q_quad(const float* P, const TfDev& tf, int i, i
   const float4 t = __ldg(reinterpret_cast<const float4*>(P + tf.q_off + i * tf.kt) + g);
   q[0] = t.x; q[1] = t.y; q[2] = t.z; q[3] = t.w;
 }
-__device__ __forceinline__ void q_quad(const float* P, const TfDev& tf, int i, int g, float2 (&q)[4]) {
-  const float4* base = reinterpret_cast<const float4*>(P + tf.q2_off + 2 * i * tf.kt) + 2 * g;
-  const float4 a = __ldg(base), b = __ldg(base + 1);
-  q[0] = make_float2(a.x, a.y); q[1] = make_float2(a.z, a.w);
-  q[2] = make_float2(b.x, b.y); q[3] = make_float2(b.z, b.w);
-}
 
-// One row of the padded Q in registers.  T = float (one line per thread): row i as KT/4
-// float4; T = float2 (packed line pairs): row i of the duplicated table, {q, q} per entry,
-// KT/2 float4.  get(g, e) is entry 4g + e as the element type.
+
+// One row of the padded Q in registers: row i as KT/4 float4 (for one line or a packed pair).
 template <int KT, class T>
 struct QRow {
-  static constexpr int NQ = sizeof(T) == 4 ? KT / 4 : KT / 2;
+  static constexpr int NQ = KT / 4;
   float4 q[NQ];
   __device__ __forceinline__ void load(const float* __restrict__ P, const TfDev& tf, int i) {
-    const float4* base = sizeof(T) == 4 ? reinterpret_cast<const float4*>(P + tf.q_off + i * tf.kt)
-                                        : reinterpret_cast<const float4*>(P + tf.q2_off + 2 * i * tf.kt);
+    const float4* base = reinterpret_cast<const float4*>(P + tf.q_off + i * tf.kt);
 #pragma unroll
     for (int g = 0; g < NQ; ++g) q[g] = __ldg(base + g);
   }
 };
+__device__ __forceinline__ float2 bcast(float q) { return make_float2(q, q); }
 
 // Forward row: y_i = sum_j Q[i][j] v_j.  One line per thread: packed FP32x2 along the inputs,
 // {acc_even, acc_odd} += {Q[i][j], Q[i][j+1]} * {v_j, v_{j+1}}, halves added at the end.
@@ -171,19 +163,20 @@ __device__ __forceinline__ float2 post_row(const QRow<KT, float2>& r, const floa
   for (int e = 0; e < 4; ++e) acc[e] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int g = 0; g < KT / 4; ++g) {
-    const float4 a = r.q[2 * g], b = r.q[2 * g + 1];
-    acc[0] = __ffma2_rn(make_float2(a.x, a.y), v[4 * g], acc[0]);
-    acc[1] = __ffma2_rn(make_float2(a.z, a.w), v[4 * g + 1], acc[1]);
-    acc[2] = __ffma2_rn(make_float2(b.x, b.y), v[4 * g + 2], acc[2]);
-    acc[3] = __ffma2_rn(make_float2(b.z, b.w), v[4 * g + 3], acc[3]);
+    const float4 a = r.q[g];
+    acc[0] = __ffma2_rn(bcast(a.x), v[4 * g], acc[0]);
+    acc[1] = __ffma2_rn(bcast(a.y), v[4 * g + 1], acc[1]);
+    acc[2] = __ffma2_rn(bcast(a.z), v[4 * g + 2], acc[2]);
+    acc[3] = __ffma2_rn(bcast(a.w), v[4 * g + 3], acc[3]);
   }
   return __fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3]));
 }
 
-// Software pipelined over rows when two rows fit in registers (at most 8 float4 each): row
+// Software pipelined over rows when two rows fit in registers beside the line (at most 8
+// float4 each for one line, 4 for a packed pair, whose data take twice the registers): row
 // i + 1's Q loads are in flight while row i is summed.
 template <int KT, class T>
-constexpr bool kPipeQ = QRow<KT, T>::NQ <= 8;
+constexpr bool kPipeQ = QRow<KT, T>::NQ <= (sizeof(T) == 4 ? 8 : 4);
 
 template <int N, int KT, class T, class Dst>
 __device__ __forceinline__ void post_fwd_k(const T (&v)[N], const TfDev& tf, const float* __restrict__ P,
@@ -228,11 +221,11 @@ __device__ __forceinline__ void post_inv_row(const QRow<KT, float2>& r, const Sr
   const float2 y = src.get_rt(i);
 #pragma unroll
   for (int g = 0; g < KT / 4; ++g) {
-    const float4 a = r.q[2 * g], b = r.q[2 * g + 1];
-    u[4 * g] = __ffma2_rn(make_float2(a.x, a.y), y, u[4 * g]);
-    u[4 * g + 1] = __ffma2_rn(make_float2(a.z, a.w), y, u[4 * g + 1]);
-    u[4 * g + 2] = __ffma2_rn(make_float2(b.x, b.y), y, u[4 * g + 2]);
-    u[4 * g + 3] = __ffma2_rn(make_float2(b.z, b.w), y, u[4 * g + 3]);
+    const float4 a = r.q[g];
+    u[4 * g] = __ffma2_rn(bcast(a.x), y, u[4 * g]);
+    u[4 * g + 1] = __ffma2_rn(bcast(a.y), y, u[4 * g + 1]);
+    u[4 * g + 2] = __ffma2_rn(bcast(a.z), y, u[4 * g + 2]);
+    u[4 * g + 3] = __ffma2_rn(bcast(a.w), y, u[4 * g + 3]);
   }
 }
 

@@ -26,10 +26,8 @@ struct TfDev {
   uint32_t par_hi;    // bit l-32 = parity of layer l (32 <= l < 64)
   uint32_t cs_off;    // float2 index of the first (cos, sin) pair
   uint32_t q_off;     // float index of the kt x kt row-major padded Q (16-B aligned)
-  uint32_t cs2_off;   // float4 index of {c, c, s, s} per rotation (packed line pairs, n <= 32)
-  uint32_t q2_off;    // float index of Q with every entry duplicated (packed line pairs, n <= 32)
   int32_t k;          // post / dense: K (the unpadded size of Q); 0 otherwise
-  uint32_t pad[3];
+  uint32_t pad[5];
 };
 static_assert(sizeof(TfDev) == 64, "TfDev layout");
 

@@ -44,9 +44,8 @@ constexpr size_t kRangeOff = ((sizeof(SchedState) + 255) / 256) * 256;  // {0, n
 constexpr size_t kTfOff = kRangeOff + 256;                           // 2 TfDev records
 constexpr size_t kParamOff = kTfOff + 256;                            // FP32 parameters
 // A transform carries a band (at most 64 layers x 32 pairs x (cos, sin)) or a post block
-// (at most 64 x 64), never both: 4096 floats; for n <= 32 also the duplicated tables of
-// the packed line pairs (at most 64 x 16 rotations x (2 + 4) or 32 x 32 x (1 + 2) floats).
-constexpr size_t kMaxParamFloats = 2 * 6144 + 32;
+// (at most 64 x 64), never both: 4096 floats, plus alignment padding.
+constexpr size_t kMaxParamFloats = 2 * 4100 + 32;
 constexpr size_t kTileOff = kParamOff + ((kMaxParamFloats * 4 + 255) / 256) * 256;
 constexpr size_t kTileBytes = (size_t)ADJ_NOALLOC_MAX_BLOCKS * sizeof(TileDev);
 constexpr size_t kBlkOff = kTileOff + kTileBytes;
@@ -161,28 +160,6 @@ int pack_tf(const adj_1d_desc_t* d, const char* name, TfDev* rec, float* params,
     for (int i = 0; i < kt; ++i)
       for (int j = 0; j < kt; ++j)
         params[np++] = (float)((i < k && j < k) ? d->q[i * k + j] : (i == j ? 1.0 : 0.0));
-  }
-  // duplicated tables for lines processed in packed pairs (n <= 32)
-  if (d->n <= 32 && d->kind == ADJ_ADJ_PRE_BAND) {
-    while (np % 4) params[np++] = 0.f;
-    rec->cs2_off = (uint32_t)(np / 4);
-    for (int i = 0; i < rec->n_pairs; ++i) {
-      const float c = (float)std::cos(d->angles[i]), s = (float)std::sin(d->angles[i]);
-      params[np++] = c;
-      params[np++] = c;
-      params[np++] = s;
-      params[np++] = s;
-    }
-  } else if (d->n <= 32 && (d->kind == ADJ_ADJ_POST_BLOCK || d->kind == ADJ_ADJ_DENSE)) {
-    while (np % 4) params[np++] = 0.f;
-    rec->q2_off = (uint32_t)np;
-    const int kt = rec->kt, k = d->k;
-    for (int i = 0; i < kt; ++i)
-      for (int j = 0; j < kt; ++j) {
-        const float v = (float)((i < k && j < k) ? d->q[i * k + j] : (i == j ? 1.0 : 0.0));
-        params[np++] = v;
-        params[np++] = v;
-      }
   }
   *n_params = np;
   return ADJ_OK;
