@@ -216,6 +216,17 @@ void materialise(const std::vector<TfHost>& tfs, std::vector<float>* params, std
         params->push_back((float)std::cos(a));
         params->push_back((float)std::sin(a));
       }
+      // per-layer table of the kernels: n / 2 pairs a layer, 16-byte aligned
+      while (params->size() % 4) params->push_back(0.f);
+      d.csl_off = (uint32_t)(params->size() / 4);
+      for (int l = 0, a = 0; l < t.n_layers; ++l) {
+        const int np = pairs_in_layer(t.n, t.parity[l]);
+        for (int j = 0; j < t.n / 2; ++j) {
+          params->push_back(j < np ? (float)std::cos(t.angles[a + j]) : 1.f);
+          params->push_back(j < np ? (float)std::sin(t.angles[a + j]) : 0.f);
+        }
+        a += np;
+      }
     } else if (t.kind == ADJ_ADJ_POST_BLOCK || t.kind == ADJ_ADJ_DENSE) {
       d.kt = t.kt;
       d.k = t.k;

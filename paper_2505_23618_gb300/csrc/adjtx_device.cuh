@@ -42,16 +42,10 @@ __device__ __forceinline__ void core_apply(int core, T (&v)[N]) {
 // Forward: layer 0 first, (x_i, x_{i+1}) -> (c x_i - s x_{i+1}, s x_i + c x_{i+1}).
 // Inverse (A^T): last layer first, each rotation transposed.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ void load_cs(const float* P, const TfDev& tf, int idx, float& c, float& s) {
-  const float2 t = __ldg(reinterpret_cast<const float2*>(P) + tf.cs_off + idx);
-  c = t.x;
-  s = t.y;
-}
-__device__ __forceinline__ void load_cs(const float* P, const TfDev& tf, int idx, float2& c, float2& s) {
-  const float2 t = __ldg(reinterpret_cast<const float2*>(P) + tf.cs_off + idx);
-  c = make_float2(t.x, t.x);
-  s = make_float2(t.y, t.y);
-}
+// Rotation j of layer l comes from the per-layer table (TfDev::csl_off): rotations 2m and
+// 2m + 1 of a layer share one 16-byte load.  Lines of packed pairs broadcast each coefficient.
+__device__ __forceinline__ float bc(float x, float) { return x; }
+__device__ __forceinline__ float2 bc(float x, float2) { return make_float2(x, x); }
 
 // Negation written per component, so that it folds into the FP32x2 FMA consuming it (one
 // instruction less per rotation than a product with -1).  The inverse keeps the product form:
@@ -59,21 +53,27 @@ __device__ __forceinline__ void load_cs(const float* P, const TfDev& tf, int idx
 __device__ __forceinline__ float rneg(float a) { return -a; }
 __device__ __forceinline__ float2 rneg(float2 a) { return make_float2(-a.x, -a.y); }
 
+template <bool INV, class T>
+__device__ __forceinline__ void rotate(T& x, T& y, T c, T s) {
+  const T a = x, b = y;
+  if (!INV) {
+    x = vfma(c, a, rneg(vmulv(s, b)));
+    y = vfma(c, b, vmulv(s, a));
+  } else {
+    x = vfma(c, a, vmulv(s, b));
+    y = vfma(c, b, vneg(vmulv(s, a)));
+  }
+}
+
 template <int N, int PAR, bool INV, class T>
-__device__ __forceinline__ void rot_layer(T (&v)[N], const TfDev& tf, const float* __restrict__ P, int off) {
+__device__ __forceinline__ void rot_layer(T (&v)[N], const float4* __restrict__ cs) {
+  constexpr int R = (N - PAR) / 2;  // rotations of the layer
 #pragma unroll
-  for (int p = 0; p < (N - PAR) / 2; ++p) {
-    const int i = 2 * p + PAR;
-    T c, s;
-    load_cs(P, tf, off + p, c, s);
-    const T x = v[i], y = v[i + 1];
-    if (!INV) {
-      v[i] = vfma(c, x, rneg(vmulv(s, y)));
-      v[i + 1] = vfma(c, y, vmulv(s, x));
-    } else {
-      v[i] = vfma(c, x, vmulv(s, y));
-      v[i + 1] = vfma(c, y, vneg(vmulv(s, x)));
-    }
+  for (int m = 0; m < (R + 1) / 2; ++m) {
+    const float4 t = __ldg(cs + m);
+    const T z{};
+    rotate<INV>(v[4 * m + PAR], v[4 * m + PAR + 1], bc(t.x, z), bc(t.y, z));
+    if (2 * m + 1 < R) rotate<INV>(v[4 * m + PAR + 2], v[4 * m + PAR + 3], bc(t.z, z), bc(t.w, z));
   }
 }
 
@@ -83,26 +83,21 @@ __device__ __forceinline__ int layer_parity(const TfDev& tf, int l) {
 
 template <int N, bool INV, class T>
 __device__ __forceinline__ void band(T (&v)[N], const TfDev& tf, const float* __restrict__ P) {
+  const float4* cs = reinterpret_cast<const float4*>(P) + tf.csl_off;
   if (!INV) {
-    int off = 0;
     for (int l = 0; l < tf.n_layers; ++l) {
       if (layer_parity(tf, l) == 0) {
-        rot_layer<N, 0, false>(v, tf, P, off);
-        off += N / 2;
+        rot_layer<N, 0, false>(v, cs + l * (N / 4));
       } else {
-        rot_layer<N, 1, false>(v, tf, P, off);
-        off += N / 2 - 1;
+        rot_layer<N, 1, false>(v, cs + l * (N / 4));
       }
     }
   } else {
-    int off = tf.n_pairs;
     for (int l = tf.n_layers - 1; l >= 0; --l) {
       if (layer_parity(tf, l) == 0) {
-        off -= N / 2;
-        rot_layer<N, 0, true>(v, tf, P, off);
+        rot_layer<N, 0, true>(v, cs + l * (N / 4));
       } else {
-        off -= N / 2 - 1;
-        rot_layer<N, 1, true>(v, tf, P, off);
+        rot_layer<N, 1, true>(v, cs + l * (N / 4));
       }
     }
   }

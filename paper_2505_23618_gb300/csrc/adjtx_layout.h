@@ -24,10 +24,13 @@ struct TfDev {
   int32_t kt;         // post: padded block size (power of two, 4 <= kt <= n)
   uint32_t par_lo;    // bit l = parity of layer l (l < 32)
   uint32_t par_hi;    // bit l-32 = parity of layer l (32 <= l < 64)
-  uint32_t cs_off;    // float2 index of the first (cos, sin) pair
+  uint32_t cs_off;    // float2 index of the first (cos, sin) pair (layers back to back)
   uint32_t q_off;     // float index of the kt x kt row-major padded Q (16-B aligned)
   int32_t k;          // post / dense: K (the unpadded size of Q); 0 otherwise
-  uint32_t pad[5];
+  uint32_t csl_off;   // float4 index of the per-layer table: layer l's (cos, sin) pairs at
+                      // float4 csl_off + l * n / 4, two rotations a float4, an odd layer
+                      // padded with one unused pair
+  uint32_t pad[4];
 };
 static_assert(sizeof(TfDev) == 64, "TfDev layout");
 

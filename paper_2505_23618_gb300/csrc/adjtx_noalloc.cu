@@ -43,9 +43,10 @@ constexpr size_t kSchedOff = 0;                                     // SchedStat
 constexpr size_t kRangeOff = ((sizeof(SchedState) + 255) / 256) * 256;  // {0, n_tiles}
 constexpr size_t kTfOff = kRangeOff + 256;                           // 2 TfDev records
 constexpr size_t kParamOff = kTfOff + 256;                            // FP32 parameters
-// A transform carries a band (at most 64 layers x 32 pairs x (cos, sin)) or a post block
-// (at most 64 x 64), never both: 4096 floats, plus alignment padding.
-constexpr size_t kMaxParamFloats = 2 * 4100 + 32;
+// A transform carries a band or a post block, never both.  A band has at most 64 layers x 32
+// (cos, sin) pairs, stored twice (back to back, and per layer padded to n / 2 pairs): 8192
+// floats; a post block at most 64 x 64 = 4096.  Plus alignment padding.
+constexpr size_t kMaxParamFloats = 2 * 8200 + 32;
 constexpr size_t kTileOff = kParamOff + ((kMaxParamFloats * 4 + 255) / 256) * 256;
 constexpr size_t kTileBytes = (size_t)ADJ_NOALLOC_MAX_BLOCKS * sizeof(TileDev);
 constexpr size_t kBlkOff = kTileOff + kTileBytes;
@@ -137,6 +138,17 @@ int pack_tf(const adj_1d_desc_t* d, const char* name, TfDev* rec, float* params,
       if (!std::isfinite(d->angles[i])) return err(ADJ_ERR_PARAM_MISMATCH, "%s: non-finite angle", name);
       params[np++] = (float)std::cos(d->angles[i]);
       params[np++] = (float)std::sin(d->angles[i]);
+    }
+    // per-layer table of the kernels: n / 2 (cos, sin) pairs a layer, 16-byte aligned
+    while (np % 4) params[np++] = 0.f;
+    rec->csl_off = (uint32_t)(np / 4);
+    for (int l = 0, a = 0; l < d->n_layers; ++l) {
+      const int lp = d->layer_parity[l] ? d->n / 2 - 1 : d->n / 2;
+      for (int j = 0; j < d->n / 2; ++j) {
+        params[np++] = j < lp ? (float)std::cos(d->angles[a + j]) : 1.f;
+        params[np++] = j < lp ? (float)std::sin(d->angles[a + j]) : 0.f;
+      }
+      a += lp;
     }
   } else if (d->kind == ADJ_ADJ_POST_BLOCK || d->kind == ADJ_ADJ_DENSE) {
     const int k = d->k;
