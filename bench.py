@@ -728,7 +728,7 @@ def run_fused(args):
             "config": {"workload": wl.name, "coefs_per_gpu": coefs, "blocks_per_gpu": nb,
                        "tiles": info["n_tiles"], "grid": info["grid_fwd"], "threads": info["threads"],
                        "tuning": {"autotune_evals": args.autotune, "ctas_per_sm": tuning["ctas_per_sm"],
-                                  "ranges_per_sm": tuning["ranges_per_sm"],
+                                  "ranges_per_sm": tuning["ranges_per_sm"], "tail_pct": tuning["tail_pct"],
                                   "cap_div": {f"{4 << (i // 5)}x{4 << (i % 5)}": d
                                               for i, d in enumerate(tuning["cap_div"]) if d != 1}},
                        "launch": "one CUDA graph per direction around the persistent kernel",

@@ -99,11 +99,16 @@ typedef struct adj_plan adj_plan_t;
 /* Launch and tiling choices of a plan (see adj_plan_autotune).
  * cap_div[(log2 w - 2) * 5 + (log2 h - 2)]: a tile of w x h blocks holds 1/cap_div of the
  * most that fit (1, 2, 4 or 8); ctas_per_sm: persistent CTAs per SM (0 = as many as fit);
- * ranges_per_sm: scheduling ranges of the class-sorted tile list per SM (1..4). */
+ * ranges_per_sm: scheduling ranges of the class-sorted tile list per SM (1..4);
+ * tail_pct: the cheapest tiles, this percentage of the estimated run time, are dealt over
+ * the ends of all ranges instead of staying with their class (0..50), so that the tiles
+ * CTAs hold when the work runs out are short ones.  A new plan has every cap_div 1,
+ * ctas_per_sm 0, ranges_per_sm 1 and tail_pct 10. */
 typedef struct {
   int32_t cap_div[25];
   int32_t ctas_per_sm;
   int32_t ranges_per_sm;
+  int32_t tail_pct;
 } adj_tuning_t;
 
 /* Plan flags. */
@@ -384,7 +389,7 @@ int adj_plan_set_tuning(adj_plan_t* plan, const adj_tuning_t* tuning);
 /*
  * Autotuner: times forward + inverse on the plan's own blocks (d_resid int16 input,
  * d_coef and d_recon FP32 scratch of total_coefs samples, all device) for candidate
- * tunings and keeps the fastest: CTAs per SM, ranges per SM, then the tile capacity of each
+ * tunings and keeps the fastest: the tail share, CTAs per SM, ranges per SM, then the tile capacity of each
  * block size in order of its share of the coefficients (coordinate descent).  If
  * cache_path is given, a result stored there for this device and this workload signature
  * (block sizes and transform kinds) is applied without measuring, and a new result is

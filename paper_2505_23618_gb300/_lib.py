@@ -49,7 +49,8 @@ class Adj1dDesc(C.Structure):
 
 
 class AdjTuning(C.Structure):
-    _fields_ = [("cap_div", C.c_int32 * 25), ("ctas_per_sm", C.c_int32), ("ranges_per_sm", C.c_int32)]
+    _fields_ = [("cap_div", C.c_int32 * 25), ("ctas_per_sm", C.c_int32), ("ranges_per_sm", C.c_int32),
+                ("tail_pct", C.c_int32)]
 
 
 class AdjPlanInfo(C.Structure):
@@ -266,13 +267,15 @@ class Plan:
     def tuning(self) -> dict:
         t = AdjTuning()
         check(self._lib.adj_plan_get_tuning(self._h, C.byref(t)))
-        return {"cap_div": list(t.cap_div), "ctas_per_sm": t.ctas_per_sm, "ranges_per_sm": t.ranges_per_sm}
+        return {"cap_div": list(t.cap_div), "ctas_per_sm": t.ctas_per_sm, "ranges_per_sm": t.ranges_per_sm,
+                "tail_pct": t.tail_pct}
 
     def set_tuning(self, tuning: dict):
         t = AdjTuning()
         t.cap_div[:] = list(tuning["cap_div"])
         t.ctas_per_sm = int(tuning["ctas_per_sm"])
         t.ranges_per_sm = int(tuning["ranges_per_sm"])
+        t.tail_pct = int(tuning.get("tail_pct", self.tuning()["tail_pct"]))
         check(self._lib.adj_plan_set_tuning(self._h, C.byref(t)))
 
     def autotune(self, d_in, d_coef, d_recon, cache_path=None, max_evals=0, stream=None):

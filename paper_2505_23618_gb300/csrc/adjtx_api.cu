@@ -491,6 +491,10 @@ struct TileSet {
   int n_ranges = 0;
 };
 
+// Default share (percent of the estimated cost) of the cheapest tiles that are dealt over the
+// ends of the per-SM ranges (adj_tuning_t::tail_pct).
+constexpr int kDefaultTailPct = 10;
+
 // Estimated run time of a tile in the fused kernel (microseconds on GB300 at 6 CTAs per SM),
 // a least-squares fit of measured tile times on a mixed workload: a fixed cost per tile;
 // per line, an extra cost for 64-sample lines (one line per thread, no packed pairs) and for
@@ -594,16 +598,50 @@ void build_tiles(const adj_plan* p, size_t i0, size_t i1, TileSet* ts) {
   std::vector<unsigned>& rbeg = ts->rbeg;
   const size_t r0 = rbeg.size();  // this set's first range entry (ts may hold earlier sets)
   if (n_ranges > 0) {
-    std::vector<double> cum(nt + 1, 0.0);
-    for (size_t i = 0; i < nt; ++i) cum[i + 1] = cum[i] + tile_cost(p, tiles[first_tile + i]);
-    rbeg.push_back(0);
-    for (int r = 1; r < n_ranges; ++r) {
-      const double target = cum.back() * r / n_ranges;
-      size_t i = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
-      i = std::max<size_t>(i, rbeg.back());
-      rbeg.push_back((unsigned)std::min(i, nt));
+    // The cheapest tiles, tail_pct percent of the estimated cost, are dealt over the ends of
+    // all ranges: whichever tiles a CTA still holds when the work runs out are then short
+    // ones, whatever classes its range holds.  The other tiles are cut into ranges in class
+    // order.  Both parts are cut on their cumulative cost.
+    std::vector<double> cost(nt);
+    double total = 0.0;
+    for (size_t i = 0; i < nt; ++i) total += (cost[i] = tile_cost(p, tiles[first_tile + i]));
+    std::vector<char> in_tail(nt, 0);
+    if (p->tuning.tail_pct > 0) {
+      std::vector<size_t> by_cost(nt);
+      for (size_t i = 0; i < nt; ++i) by_cost[i] = i;
+      std::stable_sort(by_cost.begin(), by_cost.end(), [&](size_t x, size_t y) { return cost[x] < cost[y]; });
+      const double budget = total * p->tuning.tail_pct / 100.0;
+      double acc = 0.0;
+      for (size_t i : by_cost) {
+        if (acc + cost[i] > budget) break;
+        acc += cost[i];
+        in_tail[i] = 1;
+      }
     }
-    rbeg.push_back((unsigned)nt);
+    std::vector<size_t> part[2];
+    for (size_t i = 0; i < nt; ++i) part[in_tail[i]].push_back(i);
+    // range boundaries of each part, cut on the part's cumulative cost
+    std::vector<size_t> bounds[2];
+    for (int q = 0; q < 2; ++q) {
+      const std::vector<size_t>& idx = part[q];
+      std::vector<double> cum(idx.size() + 1, 0.0);
+      for (size_t i = 0; i < idx.size(); ++i) cum[i + 1] = cum[i] + cost[idx[i]];
+      bounds[q].push_back(0);
+      for (int r = 1; r < n_ranges; ++r) {
+        const size_t i = std::lower_bound(cum.begin(), cum.end(), cum.back() * r / n_ranges) - cum.begin();
+        bounds[q].push_back(std::max(bounds[q].back(), std::min(i, idx.size())));
+      }
+      bounds[q].push_back(idx.size());
+    }
+    std::vector<TileDev> order;
+    order.reserve(nt);
+    rbeg.push_back(0);
+    for (int r = 0; r < n_ranges; ++r) {
+      for (int q = 0; q < 2; ++q)
+        for (size_t i = bounds[q][r]; i < bounds[q][r + 1]; ++i) order.push_back(tiles[first_tile + part[q][i]]);
+      rbeg.push_back((unsigned)order.size());
+    }
+    std::copy(order.begin(), order.end(), tiles.begin() + first_tile);
   }
   // Within each range the most expensive tiles go first (ties keep the class order), so the
   // tiles still queued when the ranges run dry are the short ones.
@@ -972,6 +1010,7 @@ int adj_plan_create(adj_plan_t** plan, const adj_1d_desc_t* tfs, int32_t n_tfs, 
     for (int i = 0; i < 25; ++i) p->tuning.cap_div[i] = 1;
     p->tuning.ctas_per_sm = 0;
     p->tuning.ranges_per_sm = 1;
+    p->tuning.tail_pct = kDefaultTailPct;
     apply_grid(p);
   }
   if (rc) return rc;
@@ -1038,6 +1077,7 @@ int adj_layout_preview(const adj_1d_desc_t* tfs, int32_t n_tfs, const adj_block_
   for (int i = 0; i < 25; ++i) pl.tuning.cap_div[i] = 1;
   pl.tuning.ctas_per_sm = 0;
   pl.tuning.ranges_per_sm = 1;
+  pl.tuning.tail_pct = kDefaultTailPct;
   pl.n_sm = n_sm;
   TileSet ts;
   build_tiles(&pl, 0, pl.blocks.size(), &ts);
@@ -1249,6 +1289,7 @@ int adj_plan_set_tuning(adj_plan_t* p, const adj_tuning_t* t) try {
       return fail(ADJ_ERR_INVALID_ARG, "cap_div[%d] = %d", i, t->cap_div[i]);
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return fail(ADJ_ERR_INVALID_ARG, "ctas_per_sm %d", t->ctas_per_sm);
   if (t->ranges_per_sm < 1 || t->ranges_per_sm > 4) return fail(ADJ_ERR_INVALID_ARG, "ranges_per_sm %d", t->ranges_per_sm);
+  if (t->tail_pct < 0 || t->tail_pct > 50) return fail(ADJ_ERR_INVALID_ARG, "tail_pct %d", t->tail_pct);
   p->tuning = *t;
   apply_grid(p);
   if (p->has_blocks) return build_layout(p);
@@ -1292,7 +1333,7 @@ std::string device_name(int dev) {
   return s;
 }
 
-// Cache lines: "<device> <signature hex> <ctas> <ranges> <25 cap_div>"
+// Cache lines: "<device> <signature hex> <ctas> <ranges> <tail_pct> <25 cap_div>"
 bool cache_lookup(const char* path, const std::string& dev, uint64_t sig, adj_tuning_t* t) {
   if (!path) return false;
   FILE* f = fopen(path, "r");
@@ -1301,7 +1342,7 @@ bool cache_lookup(const char* path, const std::string& dev, uint64_t sig, adj_tu
   unsigned long long s;
   adj_tuning_t c{};
   bool found = false;
-  while (fscanf(f, "%255s %llx %d %d", name, &s, &c.ctas_per_sm, &c.ranges_per_sm) == 4) {
+  while (fscanf(f, "%255s %llx %d %d %d", name, &s, &c.ctas_per_sm, &c.ranges_per_sm, &c.tail_pct) == 5) {
     bool ok = true;
     for (int i = 0; i < 25 && ok; ++i) ok = fscanf(f, "%d", &c.cap_div[i]) == 1;
     if (!ok) break;
@@ -1318,7 +1359,7 @@ void cache_store(const char* path, const std::string& dev, uint64_t sig, const a
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %llx %d %d", dev.c_str(), (unsigned long long)sig, t.ctas_per_sm, t.ranges_per_sm);
+  fprintf(f, "%s %llx %d %d %d", dev.c_str(), (unsigned long long)sig, t.ctas_per_sm, t.ranges_per_sm, t.tail_pct);
   for (int i = 0; i < 25; ++i) fprintf(f, " %d", t.cap_div[i]);
   fprintf(f, "\n");
   fclose(f);
@@ -1384,7 +1425,14 @@ int adj_plan_autotune(adj_plan_t* p, const int16_t* x, float* y, float* xr, cons
     }
     return ADJ_OK;
   };
-  // persistent CTAs per SM, then ranges per SM
+  // share of the cheapest tiles dealt over the ends of the ranges, then persistent CTAs per
+  // SM, then ranges per SM
+  for (int tp : {0, 5, 10, 20}) {
+    if (tp == best.tail_pct) continue;
+    adj_tuning_t cand = best;
+    cand.tail_pct = tp;
+    if ((rc = trial(cand))) return rc;
+  }
   const int occ = std::min(p->occ_fwd, p->occ_inv);
   for (int c = occ - 1; c >= std::max(2, occ - 2); --c) {
     adj_tuning_t cand = best;

@@ -529,7 +529,7 @@ __device__ __forceinline__ void multi_after_rows(const TfDev& th, const TfDev& t
 // the Multiple and frame modes); the register budget follows from it, so spills are never
 // traded for occupancy that shared memory forbids.
 constexpr int fused_static_smem(bool aux) {
-  return 3 * (kMaxTileBlocks + 4) * 4 + (aux ? 3 * (kMaxTileBlocks + 4) * 4 : 16) + 4 * 64 + 4 * 16 + 64;
+  return 2 * (kMaxTileBlocks + 4) * 4 + (aux ? 2 * (kMaxTileBlocks + 4) * 4 : 16) + 4 * 64 + 2 * 16 + 64;
 }
 constexpr int fused_ctas_per_sm(bool inverse, int mode) {
   return kSmemPerSm / (fused_dyn_smem(inverse, mode) +
@@ -556,22 +556,23 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
   static_assert(!(INV && MODE == kModePackedF32), "FP32 input is the inverse's own");
   static_assert(INV || MODE != kModeFrameI16, "int16 output is for the inverse");
   extern __shared__ __align__(16) unsigned char smem[];
-  // Records of this CTA's tiles, by the tile's sequence number k in the CTA:
-  //   sDesc[k % 4]   descriptor (k .. k+2 are valid at the top of iteration k; k+3 arrives)
-  //   sOff[k % 3]    block offsets / 16 (k, k+1 valid; k+2 arrives); a tile's list starts at
-  //                  entry blk_begin & 3 (it is copied from the 16-byte aligned address below)
-  //   sTf[k % 2]     (horizontal, vertical) transform records (k valid; k+1 arrives)
-  //   sAux[k % 3]    Multiple / frame modes: side or frame offsets / 4, indexed like sOff
-  //                  (k valid; k+1 arrives; the frame forward also needs k+1 for staging)
-  // Tile data: FP32 input is staged in place, tile k in buffer k % 2 while tile k+1 is copied
-  // into the other one.  int16 input has one tile buffer and one int16 staging buffer S: the
-  // row pass of tile k reads S and writes the buffer, then tile k+1 is copied into S while the
-  // column pass of tile k runs.
-  __shared__ __align__(16) uint32_t sOff[3][kMaxTileBlocks + 4];
-  __shared__ __align__(16) uint32_t sAux[AUX ? 3 : 1][AUX ? kMaxTileBlocks + 4 : 4];
+  // Records of this CTA's tiles, by the tile's sequence number k in the CTA, in slot k % 2:
+  //   sDesc   descriptor of tile k+1: fetched at step (5) of iteration k-1, valid from (1) of k
+  //   sOff    block offsets / 16 of tile k+1: fetched at (2) of k, valid from (4) of k; a
+  //           tile's list starts at entry blk_begin & 3 (it is copied from the 16-byte aligned
+  //           address below it)
+  //   sAux    Multiple / frame modes: side or frame offsets / 4, like sOff
+  //   sTf     (horizontal, vertical) transform records of tile k+1, like sOff
+  // Tile data: FP32 input is staged in place, tile k in buffer k % 2; int16 input has one tile
+  // buffer and one int16 staging buffer S.  Tile k+1 is copied in at step (5) of iteration k,
+  // while the column pass of tile k runs.  The claim of tile k+2 is issued at (2) and read at
+  // (5) of iteration k, so a CTA holds at most two tiles beyond the one it transforms when the
+  // work runs out (each stage of a tile's records is a dependent fetch, hidden behind a pass).
+  __shared__ __align__(16) uint32_t sOff[2][kMaxTileBlocks + 4];
+  __shared__ __align__(16) uint32_t sAux[AUX ? 2 : 1][AUX ? kMaxTileBlocks + 4 : 4];
   __shared__ __align__(16) TfDev sTf[2][2];
-  __shared__ __align__(16) TileDev sDesc[4];
-  __shared__ int sIdx[3];
+  __shared__ __align__(16) TileDev sDesc[2];
+  __shared__ int sIdx[2];
   int16_t* const S = reinterpret_cast<int16_t*>(smem + kBufBytes);  // int16 input only
   const int tid = threadIdx.x;
   Claimer cl;  // used by warp 0 only
@@ -587,27 +588,25 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
     }
   };
 
-  // Prologue: warp 0 claims three tiles and puts a claim for a fourth in flight; fetch the records
-  // of tile 0, stage it, and start fetching the offsets of tile 1 and the descriptor of tile 2.
+  // Prologue: warp 0 claims two tiles; fetch the records of tile 0 and the descriptor of tile
+  // 1, and stage tile 0.
   if (tid < 32) {
     const int t0 = cl.grab(a.sched, a.range_begin, a.n_ranges);
     const int t1 = t0 >= 0 ? cl.grab(a.sched, a.range_begin, a.n_ranges) : -1;
-    const int t2 = t1 >= 0 ? cl.grab(a.sched, a.range_begin, a.n_ranges) : -1;
-    if (t2 >= 0) cl.issue(a.sched);
     if (tid == 0) {
       sIdx[0] = t0;
       sIdx[1] = t1;
-      sIdx[2] = t2;
     }
   }
   __syncthreads();
-  int t = sIdx[0], tn = sIdx[1], tn2 = sIdx[2];
+  int t = sIdx[0], tn = sIdx[1];
   if (t >= 0) {
     const TileDev d0 = a.tiles[t];
     if (tid == 0) {
       sDesc[0] = d0;
       sTf[0][0] = a.tfs[d0.tf_h];
       sTf[0][1] = a.tfs[d0.tf_v];
+      if (tn >= 0) sDesc[1] = a.tiles[tn];
     }
     for (int b = tid; b < d0.nblk; b += THREADS) sOff[0][(d0.blk_begin & 3) + b] = a.tile_blk[d0.blk_begin + b];
     if constexpr (AUX) {
@@ -615,48 +614,33 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
     }
     __syncthreads();
     stage(d0, 0, reinterpret_cast<float*>(smem));
-    if (tn >= 0) {
-      const TileDev d1 = a.tiles[tn];
-      if (tid == 0) sDesc[1] = d1;
-      copy_async<THREADS>(sOff[1], a.tile_blk + (d1.blk_begin & ~3u), list_bytes(d1));
-      if constexpr (AUX) copy_async<THREADS>(sAux[1], a.tile_aux + (d1.blk_begin & ~3u), list_bytes(d1));
-    }
-    if (tn2 >= 0 && tid == 0) cp_async16(&sDesc[2], a.tiles + tn2);
     cp_async_commit();
   }
 
-  // Per tile k: (1) wait for everything fetched during the previous iteration, barrier;
-  // (2) FP32 input: start copying tile k+1 into the other buffer; both: fetch the transform
-  // records of tile k+1 and the offsets of tile k+2; warp 0 reads the claim issued an
-  // iteration ago (tile k+3), fetches that tile's descriptor and issues the claim of tile k+4;
-  // (3) row pass; (4) barrier; int16 input: start copying tile k+1 into S; (5) column pass.
-  for (int k = 0; t >= 0; ++k) {
+  // Per tile k: (1) wait for the copies issued so far, barrier; (2) fetch the block offsets
+  // and transform records of tile k+1 (whose descriptor has arrived); warp 0 issues the claim
+  // of tile k+2; (3) row pass; (4) wait, barrier; (5) start copying tile k+1's input; warp 0
+  // reads the claim of tile k+2 and fetches its descriptor; column pass.
+  for (int k = 0;; ++k) {
     const int cur = F32_IN ? (k & 1) : 0;
     float* buf = reinterpret_cast<float*>(smem + cur * kBufBytes);
     // (1)
     cp_async_wait_all();
     __syncthreads();
-    const TileDev td = sDesc[k & 3];
+    if (k > 0) {
+      t = tn;
+      tn = sIdx[0];
+    }
+    if (t < 0) break;
+    const TileDev td = sDesc[k & 1];
     // (2)
     if (tn >= 0) {
-      const TileDev dn = sDesc[(k + 1) & 3];
-      if constexpr (F32_IN) stage(dn, (k + 1) % 3, reinterpret_cast<float*>(smem + (cur ^ 1) * kBufBytes));
+      const TileDev dn = sDesc[(k + 1) & 1];
+      copy_async<THREADS>(sOff[(k + 1) & 1], a.tile_blk + (dn.blk_begin & ~3u), list_bytes(dn));
+      if constexpr (AUX) copy_async<THREADS>(sAux[(k + 1) & 1], a.tile_aux + (dn.blk_begin & ~3u), list_bytes(dn));
       copy_async<THREADS>(&sTf[(k + 1) & 1][0], a.tfs + dn.tf_h, sizeof(TfDev));
       copy_async<THREADS>(&sTf[(k + 1) & 1][1], a.tfs + dn.tf_v, sizeof(TfDev));
-    }
-    if (tn2 >= 0) {
-      const TileDev dn2 = sDesc[(k + 2) & 3];
-      copy_async<THREADS>(sOff[(k + 2) % 3], a.tile_blk + (dn2.blk_begin & ~3u), list_bytes(dn2));
-      if constexpr (AUX) copy_async<THREADS>(sAux[(k + 2) % 3], a.tile_aux + (dn2.blk_begin & ~3u), list_bytes(dn2));
-    }
-    // sIdx[0] is free: every thread read it after the previous iteration's barrier (4)
-    if (tid < 32) {
-      const int t3 = tn2 >= 0 ? cl.resolve(a.sched, a.range_begin, a.n_ranges) : -1;
-      if (t3 >= 0) cl.issue(a.sched);
-      if (tid == 0) {
-        sIdx[0] = t3;
-        if (t3 >= 0) cp_async16(&sDesc[(k + 3) & 3], a.tiles + t3);
-      }
+      if (tid < 32) cl.issue(a.sched);
     }
     cp_async_commit();
 
@@ -684,18 +668,27 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
       }
     }
     // (4)
+    cp_async_wait_all();
     __syncthreads();
-    const int tn3 = sIdx[0];
-    if constexpr (!F32_IN) {
-      if (tn >= 0) {
-        stage(sDesc[(k + 1) & 3], (k + 1) % 3, nullptr);
-        cp_async_commit();
+    // (5)
+    if (tn >= 0) {
+      stage(sDesc[(k + 1) & 1], (k + 1) & 1, reinterpret_cast<float*>(smem + (cur ^ 1) * kBufBytes));
+      if (tid < 32) {
+        const int t2 = cl.resolve(a.sched, a.range_begin, a.n_ranges);
+        // tile k+2 takes the descriptor slot of tile k, which every thread has read at (1)
+        if (tid == 0) {
+          sIdx[0] = t2;
+          if (t2 >= 0) cp_async16(&sDesc[k & 1], a.tiles + t2);
+        }
       }
+    } else if (tid == 0) {
+      sIdx[0] = -1;
     }
-    // (5) column pass (vertical transform, length h), stores to global memory
-    const uint32_t* offs = sOff[k % 3] + (td.blk_begin & 3);
+    cp_async_commit();
+    // column pass (vertical transform, length h), stores to global memory
+    const uint32_t* offs = sOff[k & 1] + (td.blk_begin & 3);
     if constexpr (MULTI) {
-      const uint32_t* sides = sAux[k % 3] + (td.blk_begin & 3);
+      const uint32_t* sides = sAux[k & 1] + (td.blk_begin & 3);
       const TfDev th = sTf[k & 1][0], tv = sTf[k & 1][1];
       switch (h) {
         case 4: multi_after_rows<4, THREADS>(th, tv, a.params, buf, offs, sides, a.out, a.side, nb, w); break;
@@ -706,7 +699,7 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
       }
     } else {
       const TfDev tf = sTf[k & 1][1];
-      const uint32_t* aux = sAux[AUX ? k % 3 : 0] + (td.blk_begin & 3);
+      const uint32_t* aux = sAux[AUX ? (k & 1) : 0] + (td.blk_begin & 3);
       const int st = (int)a.frame_stride;
       switch (h) {
         case 4: col_dispatch<4, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
@@ -716,9 +709,6 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
         default: col_dispatch<64, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
       }
     }
-    t = tn;
-    tn = tn2;
-    tn2 = tn3;
   }
   cp_async_wait_all();
 
