@@ -27,13 +27,26 @@ __device__ __forceinline__ float2 vmulv(float2 a, float2 b) { return __fmul2_rn(
 // Fast cores (Section 2.1).  Cores 0..3 are DCT-2, DCT-3, DST-2, DST-3; the inverse of
 // each is its transpose, which is the core with index c ^ 1.
 // ---------------------------------------------------------------------------------
-template <int N, class T>
+// PAIR64: 64-point lines run the packed-pair form of the cores (two 32-point cores in one
+// FP32x2 pass and a prefix chain: 340 instead of 600 instructions).  It needs a few more live
+// registers than the scalar flow graph, which the 168-register kernels have and the
+// 128-register int16-input kernels do not, so those keep the scalar graph.
+template <int N, bool PAIR64 = false, class T>
 __device__ __forceinline__ void core_apply(int core, T (&v)[N]) {
-  switch (core) {
-    case 0: Core<N, 0>::apply(v); break;
-    case 1: Core<N, 1>::apply(v); break;
-    case 2: Core<N, 2>::apply(v); break;
-    default: Core<N, 3>::apply(v); break;
+  if constexpr (N == 64 && PAIR64) {
+    switch (core) {
+      case 0: CorePair64<0>::apply(v); break;
+      case 1: CorePair64<1>::apply(v); break;
+      case 2: CorePair64<2>::apply(v); break;
+      default: CorePair64<3>::apply(v); break;
+    }
+  } else {
+    switch (core) {
+      case 0: Core<N, 0>::apply(v); break;
+      case 1: Core<N, 1>::apply(v); break;
+      case 2: Core<N, 2>::apply(v); break;
+      default: Core<N, 3>::apply(v); break;
+    }
   }
 }
 
@@ -480,7 +493,7 @@ __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __r
     }
   } else {
     if (tf.kind >= KIND_POST) post_inv<N>(v, tf, P, src);
-    if (tf.kind != KIND_DENSE) core_apply<N>(tf.core ^ 1, v);
+    if (tf.kind != KIND_DENSE) core_apply<N, true>(tf.core ^ 1, v);
     if (tf.kind == KIND_BAND) band<N, true>(v, tf, P);
     dst.template store<N>(v);
   }

@@ -21,8 +21,25 @@ Section 2.1 of Said, Egilmez & Chao:
 R (reversal) and S (alternating sign) cost nothing: they become register
 renaming and negation modifiers that the compiler folds into the adds/FMAs.
 
-The script checks each generated graph in FP64 against its own definition of
-the orthonormal DCT-2 before writing ``cores_gen.cuh``.
+The 64-point cores run as two 32-point cores at once in packed FP32x2 arithmetic
+(one thread holds one 64-sample line, and a 32-point graph on float2 values costs the
+instructions of one 32-point line).  With a_n = x_n, b_n = x_{63-n} (n < 32):
+
+    u_n = (a_n + b_n) / sqrt(2),   y_n = sqrt(2) cos(pi (2n+1) / 128) (a_n - b_n),
+    (U, Y) = DCT2_32 of (u, y), both lanes of one packed pass,
+    X_{2k} = U_k,   X_1 = Y_0 / sqrt(2),   X_{2k+1} = Y_k - X_{2k-1}  (k >= 1).
+
+The last line follows from 2 cos(A) cos(B) = cos(A + B) + cos(A - B): the DCT-2 of the
+cosine-weighted differences is the sum of neighbouring odd outputs of the DCT-2 of x, so a
+prefix chain of 31 subtractions recovers them.  O_k is an alternating sum of k + 1 outputs of
+the 32-point core, so their rounding errors add up: at most about 1.5e-6 of the line norm in
+FP32, against 2e-7 for the flow graphs (tests/test_cores_fp32.py).  DCT-3 is the transpose
+(the chain runs backwards); DST-2 / DST-3 fold the R / S maps into the constants of the first
+step and the output (input) order.  The packed cores are emitted as CorePair64 beside the
+scalar flow graphs of Core<64, c>; the kernels choose per direction.
+
+The script checks each generated graph, and the structure of the packed 64-point cores, in
+FP64 against its own definition of the orthonormal DCT-2 before writing ``cores_gen.cuh``.
 """
 
 from __future__ import annotations
@@ -43,6 +60,7 @@ class Graph:
     ('add', i, j)            : (s_i, s_j) <- (s_i + s_j, s_i - s_j)
     ('mat', i, j, a, b, c, d): (s_i, s_j) <- (a s_i + b s_j, c s_i + d s_j)
     ('neg', i)               : s_i <- -s_i
+    ('scale', i, a)          : s_i <- a s_i
     """
 
     def __init__(self, n):
@@ -57,6 +75,9 @@ class Graph:
 
     def neg(self, i):
         self.ops.append(("neg", i))
+
+    def scale(self, i, a):
+        self.ops.append(("scale", i, a))
 
 
 def _dct2(g, slots, scale):
@@ -133,9 +154,48 @@ def _idft(g, cpx):
     return out
 
 
-def dct2_program(N):
+def pair64_beta(i):
+    return math.sqrt(2.0) * math.cos(math.pi * (2 * i + 1) / 128.0)
+
+
+def chain_ops():
+    """The odd outputs X_{2k+1} = O_k from the second lane Y of the packed 32-point pass:
+    O_0 = Y_0 / sqrt(2), O_k = Y_k - O_{k-1}.  Each op is ("scale", k, a): c_k <- a c_k, or
+    (d, r, s): c_d <- c_d + s c_r.  (O_k is an alternating sum of Y_0 .. Y_k, so the rounding
+    errors of the Y_j add up whatever the order of evaluation; splitting the chain into linked
+    blocks measured no more accurate.)"""
+    return [("scale", 0, 1.0 / math.sqrt(2.0))] + [(k, k - 1, -1.0) for k in range(1, 32)]
+
+
+def transposed_chain_ops():
+    """The transpose of chain_ops (for DCT-3): the ops in reverse order, c_r <- c_r + s c_d."""
+    return [op if op[0] == "scale" else (op[1], op[0], op[2]) for op in reversed(chain_ops())]
+
+
+def _dct2_64_pair(g):
+    """The 64-point DCT-2 as two 32-point DCT-2 graphs (slots 0..31 and 63..32) between a
+    first step of 2x2 maps and the chain; returns the output slots."""
+    a = 1.0 / math.sqrt(2.0)
+    for i in range(32):
+        g.mat(i, 63 - i, a, a, pair64_beta(i), -pair64_beta(i))
+    ev = _dct2(g, list(range(32)), 1.0)
+    od = _dct2(g, [63 - i for i in range(32)], 1.0)
+    for op in chain_ops():
+        if op[0] == "scale":
+            g.scale(od[op[1]], op[2])
+        else:
+            d, r, sgn = op
+            g.mat(od[r], od[d], 1.0, 0.0, sgn, 1.0)
+    out = [None] * 64
+    out[0::2] = ev
+    out[1::2] = od
+    return out
+
+
+def dct2_program(N, pair=False):
+    """The DCT-2 graph: the even/odd recursion, or (N = 64, pair) the packed-pair form."""
     g = Graph(N)
-    outs = _dct2(g, list(range(N)), 1.0)
+    outs = _dct2_64_pair(g) if pair else _dct2(g, list(range(N)), 1.0)
     return list(range(N)), g.ops, outs, [], []
 
 
@@ -150,9 +210,10 @@ def transpose_ops(ops):
     return t
 
 
-def core_program(N, core):
-    """(input slot of x_n, ops, output slot of y_k) for one of the four cores."""
-    ins, ops, outs, _, _ = dct2_program(N)
+def core_program(N, core, pair=False):
+    """(input slot of x_n, ops, output slot of y_k) for one of the four cores (pair: the
+    packed-pair form of the 64-point cores)."""
+    ins, ops, outs, _, _ = dct2_program(N, pair)
     if core == 0:                                        # DCT-2
         return ins, ops, outs
     if core == 2:                                        # DST-2 = R DCT-2 S
@@ -180,6 +241,8 @@ def simulate(N, prog):
         elif op[0] == "mat":
             _, i, j, a, b, c, d = op
             V[i], V[j] = a * V[i] + b * V[j], c * V[i] + d * V[j]
+        elif op[0] == "scale":
+            V[op[1]] = op[2] * V[op[1]]
         else:
             V[op[1]] = -V[op[1]]
     return np.stack([V[outs[k]] for k in range(N)])
@@ -196,9 +259,127 @@ def definition(N, core):
     return {0: c2, 1: c2.T, 2: s2, 3: s2.T}[core]
 
 
+def pair64_spec(core):
+    """What the packed 64-point code of `core` does (emit_pair64 writes it, simulate_pair64
+    runs it).  Forward type (DCT-2, DST-2): z_i = (ca v[ia] + cb v[ib], cc v[ia] + cd v[ib]),
+    32-point DCT-2 of both lanes, forward chain on one lane, then v[m] = z[k].lane.  Transpose
+    type (DCT-3, DST-3): z_k = (v[ix], v[iy]), backward chain on one lane, 32-point DCT-3 of
+    both lanes, then (v[oa], v[ob]) = (ca z.x + cb z.y, cc z.x + cd z.y).  The DST forms keep
+    the odd part in lane x, so that the output (input) reversal still pairs neighbouring
+    samples in one float2 (vector shared-memory stores and loads need no register moves)."""
+    a = 1.0 / math.sqrt(2.0)
+    sig = [1.0 if i % 2 == 0 else -1.0 for i in range(32)]
+    if core in (0, 2):
+        pre, out = [], {}
+        for i in range(32):
+            b = pair64_beta(i)
+            if core == 0:
+                pre.append((i, 63 - i, a, a, b, -b))
+            else:                                        # S on the input; odd part in lane x
+                s = sig[i]
+                pre.append((i, 63 - i, s * b, s * b, s * a, -s * a))
+        for k in range(32):
+            if core == 0:
+                out[2 * k], out[2 * k + 1] = (k, "x"), (k, "y")
+            else:                                        # R on the output
+                out[63 - 2 * k], out[62 - 2 * k] = (k, "y"), (k, "x")
+        return {"type": "fwd", "chain": "y" if core == 0 else "x", "pre": pre,
+                "out": [out[m] for m in range(64)]}
+    inp, post = [], []
+    for k in range(32):
+        inp.append((2 * k, 2 * k + 1) if core == 1 else (62 - 2 * k, 63 - 2 * k))
+    for i in range(32):
+        b = pair64_beta(i)
+        if core == 1:
+            post.append((i, 63 - i, a, b, a, -b))
+        else:                                            # R on the input, S on the output
+            s = sig[i]
+            post.append((i, 63 - i, s * b, s * a, s * b, -s * a))
+    return {"type": "inv", "chain": "y" if core == 1 else "x", "inp": inp, "post": post}
+
+
+def run_chain(c, ops):
+    for op in ops:
+        if op[0] == "scale":
+            c[op[1]] = op[2] * c[op[1]]
+        else:
+            c[op[0]] = c[op[0]] + op[2] * c[op[1]]
+
+
+def simulate_pair64(core):
+    """FP64 matrix of the packed 64-point code described by pair64_spec(core)."""
+    spec = pair64_spec(core)
+    a = 1.0 / math.sqrt(2.0)
+    X = np.eye(64)
+    if spec["type"] == "fwd":
+        C = simulate(32, core_program(32, 0))
+        z = {"x": np.stack([ca * X[ia] + cb * X[ib] for ia, ib, ca, cb, cc, cd in spec["pre"]]),
+             "y": np.stack([cc * X[ia] + cd * X[ib] for ia, ib, ca, cb, cc, cd in spec["pre"]])}
+        z = {l: C @ m for l, m in z.items()}
+        run_chain(z[spec["chain"]], chain_ops())
+        return np.stack([z[lane][k] for k, lane in spec["out"]])
+    C = simulate(32, core_program(32, 1))
+    z = {"x": np.stack([X[ix] for ix, iy in spec["inp"]]), "y": np.stack([X[iy] for ix, iy in spec["inp"]])}
+    run_chain(z[spec["chain"]], transposed_chain_ops())
+    zx, zy = C @ z["x"], C @ z["y"]
+    V = np.zeros((64, 64))
+    for i, (oa, ob, ca, cb, cc, cd) in enumerate(spec["post"]):
+        V[oa] = ca * zx[i] + cb * zy[i]
+        V[ob] = cc * zx[i] + cd * zy[i]
+    return V
+
+
 def f32(x):
     v = float(np.float32(x))
     return "%.9ef" % v
+
+
+def emit_chain(lane, ops):
+    out = []
+    for op in ops:
+        if op[0] == "scale":
+            out.append(f"    z[{op[1]}].{lane} = {f32(op[2])} * z[{op[1]}].{lane};")
+        else:
+            d, r, sgn = op
+            out.append(f"    z[{d}].{lane} = z[{d}].{lane} {'+' if sgn > 0 else '-'} z[{r}].{lane};")
+    return out
+
+
+def emit_pair64(core, inner_counts):
+    """Packed FP32x2 code of a 64-point core (see pair64_spec)."""
+    spec = pair64_spec(core)
+    nb, nr = inner_counts
+    a = 1.0 / math.sqrt(2.0)
+    lines = ["    static_assert(sizeof(T) == sizeof(float), \"64-sample lines are one per thread\");",
+             "    float2 z[32];"]
+    if spec["type"] == "fwd":
+        for i, (ia, ib, ca, cb, cc, cd) in enumerate(spec["pre"]):
+            lines.append(f"    z[{i}] = vpre2(v[{ia}], v[{ib}], make_float2({f32(ca)}, {f32(cc)}), "
+                         f"make_float2({f32(cb)}, {f32(cd)}));")
+        lines.append("    Core<32, 0>::apply(z);")
+        lines += emit_chain(spec["chain"], chain_ops())
+        for m, (k, lane) in enumerate(spec["out"]):
+            lines.append(f"    v[{m}] = z[{k}].{lane};")
+        name = "first step"
+    else:
+        for k, (ix, iy) in enumerate(spec["inp"]):
+            lines.append(f"    z[{k}] = make_float2(v[{ix}], v[{iy}]);")
+        lines += emit_chain(spec["chain"], transposed_chain_ops())
+        lines.append("    Core<32, 1>::apply(z);")
+        for i, (oa, ob, ca, cb, cc, cd) in enumerate(spec["post"]):
+            lines.append(f"    {{ const float2 r = vpre2(z[{i}].x, z[{i}].y, make_float2({f32(ca)}, {f32(cc)}), "
+                         f"make_float2({f32(cb)}, {f32(cd)})); v[{oa}] = r.x; v[{ob}] = r.y; }}")
+        name = "last step"
+    nc = len(chain_ops())
+    n_ins = 2 * nb + 4 * nr + 64 + nc
+    flops = 2 * (2 * nb + 6 * nr) + 6 * 32 + nc
+    head = (f"// {CORE_NAMES[core]} N=64 packed: two 32-point lines in FP32x2 ({nb} butterflies (2 FADD), "
+            f"{nr} rotations (2 FMUL + 2 FFMA) on float2), 32 {name} maps (FP32x2 FMUL + FFMA), "
+            f"{nc} chain ops = {n_ins} instructions, {flops} FP32 ops")
+    body = "\n".join(lines)
+    return (f"{head}\ntemplate <> struct CorePair64<{core}> {{\n"
+            f"  template <class T>\n"
+            f"  static __device__ __forceinline__ void apply(T (&v)[64]) {{\n{body}\n  }}\n}};\n")
 
 
 def emit(N, core, prog):
@@ -279,8 +460,10 @@ def generate() -> str:
         "// Do not edit; regenerate with `python gen_cores.py`.\n"
         "#pragma once\n\n"
         "#include \"vec_ops.cuh\"\n\n"
-        "template <int N, int CORE> struct Core;\n\n"
+        "template <int N, int CORE> struct Core;\n"
+        "template <int CORE> struct CorePair64;\n\n"
     ]
+    inner = None
     for N in SIZES:
         for core in range(4):
             prog = core_program(N, core)
@@ -288,6 +471,15 @@ def generate() -> str:
             if err > 1e-12:
                 raise AssertionError(f"graph N={N} core={core} off by {err}")
             chunks.append(emit(N, core, prog) + "\n")
+            if N == 32 and core == 0:
+                ops = prog[1]
+                inner = (sum(op[0] == "add" for op in ops), sum(op[0] == "mat" for op in ops))
+    for core in range(4):
+        for err in (np.abs(simulate(64, core_program(64, core, pair=True)) - definition(64, core)).max(),
+                    np.abs(simulate_pair64(core) - definition(64, core)).max()):
+            if err > 1e-12:
+                raise AssertionError(f"packed 64-point core {core} off by {err}")
+        chunks.append(emit_pair64(core, inner) + "\n")
     return "".join(chunks)
 
 

@@ -24,3 +24,9 @@ __device__ __forceinline__ float2 vmac(float c1, float2 a, float c2, float2 b) {
   return __ffma2_rn(make_float2(c1, c1), a, __fmul2_rn(make_float2(c2, c2), b));
 }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// (c.x a + d.x b, c.y a + d.y b) for scalars a, b broadcast to both halves: the first and last
+// steps of the packed 64-point cores, one FP32x2 multiply and one FP32x2 FMA.
+__device__ __forceinline__ float2 vpre2(float a, float b, float2 c, float2 d) {
+  return __ffma2_rn(make_float2(b, b), d, __fmul2_rn(make_float2(a, a), c));
+}

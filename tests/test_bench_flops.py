@@ -15,7 +15,12 @@ CORES = os.path.join(HERE, "..", "paper_2505_23618_gb300", "csrc", "cores_gen.cu
 
 def test_core_line_flops_match_the_generated_graphs():
     pat = re.compile(r"^// (DCT2|DCT3|DST2|DST3) N=(\d+): (\d+) butterflies \(2 FADD\), (\d+) rotations")
-    seen = set()
+    # packed 64-point cores: two 32-point graphs in FP32x2, 32 first / last step maps (3 flops
+    # a lane) and the chain ops (1 flop each)
+    pat64 = re.compile(r"^// (DCT2|DCT3|DST2|DST3) N=64 packed: two 32-point lines in FP32x2 \((\d+) "
+                       r"butterflies \(2 FADD\), (\d+) rotations .*, (\d+) chain ops = (\d+) instructions, "
+                       r"(\d+) FP32 ops$")
+    seen, packed = set(), set()
     with open(CORES) as f:
         for ln in f:
             m = pat.match(ln)
@@ -23,7 +28,12 @@ def test_core_line_flops_match_the_generated_graphs():
                 n, bfly, rot = int(m.group(2)), int(m.group(3)), int(m.group(4))
                 assert bench.CORE_LINE_FLOPS[n] == 2 * bfly + 6 * rot, (m.group(1), n)
                 seen.add((m.group(1), n))
-    assert len(seen) == 20
+            m = pat64.match(ln)
+            if m:
+                bfly, rot, nc, flops = (int(m.group(i)) for i in (2, 3, 4, 6))
+                assert flops == 2 * (2 * bfly + 6 * rot) + 6 * 32 + nc
+                packed.add(m.group(1))
+    assert len(seen) == 20 and len(packed) == 4
 
 
 def test_line_and_block_flops():
