@@ -273,6 +273,13 @@ __device__ __forceinline__ void post_inv_k(T (&v)[N], const TfDev& tf, const flo
   }
 }
 
+// The inverse post blocks of the fused kernels with KT = n / 2 on 16- to 64-sample lines run
+// over the whole tile before the line pass (post_inv_rows_tile / post_inv_cols_tile in
+// adjtx_fused.cuh); their per-line form is then not compiled into those kernels.
+__host__ __device__ constexpr bool post_inv_tiled(int kt, int n) {
+  return (n == 16 && kt == 8) || (n == 32 && kt == 16) || (n == 64 && kt == 32);
+}
+
 template <int N, class T, class Dst>
 __device__ __forceinline__ void post_fwd(const T (&v)[N], const TfDev& tf, const float* __restrict__ P,
                                          const Dst& dst) {
@@ -285,13 +292,14 @@ __device__ __forceinline__ void post_fwd(const T (&v)[N], const TfDev& tf, const
   }
 }
 
-template <int N, class T, class Src>
+// TILED: leave out the (N, KT) pairs that post_inv_tiled hands to the tile-wide form.
+template <int N, bool TILED = false, class T, class Src>
 __device__ __forceinline__ void post_inv(T (&v)[N], const TfDev& tf, const float* __restrict__ P, const Src& src) {
   switch (tf.kt) {
     case 4: post_inv_k<N, 4>(v, tf, P, src); break;
-    case 8: if constexpr (N >= 8) { post_inv_k<N, 8>(v, tf, P, src); } break;
-    case 16: if constexpr (N >= 16) { post_inv_k<N, 16>(v, tf, P, src); } break;
-    case 32: if constexpr (N >= 32) { post_inv_k<N, 32>(v, tf, P, src); } break;
+    case 8: if constexpr (N >= 8 && !(TILED && post_inv_tiled(8, N))) { post_inv_k<N, 8>(v, tf, P, src); } break;
+    case 16: if constexpr (N >= 16 && !(TILED && post_inv_tiled(16, N))) { post_inv_k<N, 16>(v, tf, P, src); } break;
+    case 32: if constexpr (N >= 32 && !(TILED && post_inv_tiled(32, N))) { post_inv_k<N, 32>(v, tf, P, src); } break;
     default: if constexpr (N >= 64) { post_inv_k<N, 64>(v, tf, P, src); } break;
   }
 }
@@ -492,7 +500,7 @@ __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __r
       dst.template store<N>(v);
     }
   } else {
-    if (tf.kind >= KIND_POST) post_inv<N>(v, tf, P, src);
+    if (tf.kind >= KIND_POST && !post_inv_tiled(tf.kt, N)) post_inv<N, true>(v, tf, P, src);
     if (tf.kind != KIND_DENSE) core_apply<N, true>(tf.core ^ 1, v);
     if (tf.kind == KIND_BAND) band<N, true>(v, tf, P);
     dst.template store<N>(v);

@@ -295,6 +295,134 @@ __device__ __forceinline__ void row_pass_s16(const TfDev& tf, const float* __res
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Inverse post block C^T over a whole tile (Section 2.2): u_j = sum_i Qp[i][j] y_i on the first
+// KT values of every line, i.e. U = Y Qp for the tile's lines at once.  Each thread computes
+// an LG-line x OG-output block with OG/2 FP32x2 accumulators per line, reading its lines' y_i
+// from the tile and row i of Qp (OG consecutive entries, 16-byte loads) once per i, so every Q
+// entry loaded serves LG lines; then all threads write their outputs back in place.
+// ---------------------------------------------------------------------------------
+template <int W, int KT, int THREADS>
+__device__ __forceinline__ void post_inv_rows_tile(const TfDev& tf, const float* __restrict__ P, float* buf,
+                                                   int nlines, int h) {
+  constexpr int SH = sw_shift(W), MK = sw_mask(W);
+  constexpr int OG = 8;                                         // outputs per thread
+  constexpr int NOG = KT / OG;                                  // output groups
+  constexpr int G = THREADS / NOG;                              // line groups
+  constexpr int LG = (kTileCoefs / W) / G;                      // lines per thread
+  static_assert(NOG * G == THREADS && LG * G == kTileCoefs / W, "post tile mapping");
+  const int og = threadIdx.x % NOG, lg = threadIdx.x / NOG;
+  float* row[LG];
+  int f[LG];
+  bool ok[LG];
+#pragma unroll
+  for (int j = 0; j < LG; ++j) {
+    const int l = lg + j * G;  // consecutive lines across the threads of a warp
+    ok[j] = l < nlines;
+    row[j] = buf + (ok[j] ? l : 0) * W;
+    f[j] = ((l & (h - 1)) >> SH) & MK;
+  }
+  float2 acc[LG][OG / 2];
+#pragma unroll
+  for (int j = 0; j < LG; ++j)
+#pragma unroll
+    for (int e = 0; e < OG / 2; ++e) acc[j][e] = make_float2(0.f, 0.f);
+  const float4* q = reinterpret_cast<const float4*>(P + tf.q_off) + og * (OG / 4);
+#pragma unroll 4
+  for (int i = 0; i < KT; ++i) {
+    float4 qi[OG / 4];
+#pragma unroll
+    for (int g = 0; g < OG / 4; ++g) qi[g] = __ldg(q + i * (KT / 4) + g);
+#pragma unroll
+    for (int j = 0; j < LG; ++j) {
+      const float y = row[j][(((i >> 2) ^ f[j]) << 2) + (i & 3)];
+      const float2 yy = make_float2(y, y);
+#pragma unroll
+      for (int g = 0; g < OG / 4; ++g) {
+        acc[j][2 * g] = __ffma2_rn(yy, make_float2(qi[g].x, qi[g].y), acc[j][2 * g]);
+        acc[j][2 * g + 1] = __ffma2_rn(yy, make_float2(qi[g].z, qi[g].w), acc[j][2 * g + 1]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < LG; ++j) {
+    if (!ok[j]) continue;
+#pragma unroll
+    for (int g = 0; g < OG / 4; ++g) {
+      const int c = og * (OG / 4) + g;  // output chunk
+      *reinterpret_cast<float4*>(row[j] + ((c ^ f[j]) << 2)) =
+          make_float4(acc[j][2 * g].x, acc[j][2 * g].y, acc[j][2 * g + 1].x, acc[j][2 * g + 1].y);
+    }
+  }
+  __syncthreads();
+}
+
+// The same along the columns: u_j = sum_i Qp[i][j] y_i down each column (rows i < KT of every
+// block), U = Qp^T Y per block.  A thread holds 4 adjacent columns (one 16-byte chunk of a row,
+// two FP32x2 lanes) x OG outputs for CPT chunks.
+template <int H, int KT, int THREADS>
+__device__ __forceinline__ void post_inv_cols_tile(const TfDev& tf, const float* __restrict__ P, float* buf,
+                                                   int nb, int w) {
+  constexpr int OG = 8;
+  constexpr int NOG = KT / OG;
+  constexpr int G = THREADS / NOG;                              // chunk-column groups
+  constexpr int CPT = (kTileCoefs / H / 4) / G;                 // chunk columns per thread
+  static_assert(NOG * G == THREADS && CPT * G == kTileCoefs / H / 4, "post tile mapping");
+  const int sh = sw_shift(w), mk = sw_mask(w), cpr = w >> 2, lgc = lg2(cpr);
+  const int og = threadIdx.x % NOG, cg = threadIdx.x / NOG;
+  const int nchunks = nb * cpr;
+  float* base[CPT];
+  int cq[CPT];
+  bool ok[CPT];
+#pragma unroll
+  for (int u = 0; u < CPT; ++u) {
+    const int x = cg + u * G;
+    ok[u] = x < nchunks;
+    const int b = ok[u] ? x >> lgc : 0;
+    cq[u] = x & (cpr - 1);
+    base[u] = buf + b * (w * H);
+  }
+  float2 acc[CPT][OG][2];
+#pragma unroll
+  for (int u = 0; u < CPT; ++u)
+#pragma unroll
+    for (int o = 0; o < OG; ++o) acc[u][o][0] = acc[u][o][1] = make_float2(0.f, 0.f);
+  const float4* q = reinterpret_cast<const float4*>(P + tf.q_off) + og * (OG / 4);
+#pragma unroll 4
+  for (int i = 0; i < KT; ++i) {
+    float qs[OG];
+#pragma unroll
+    for (int g = 0; g < OG / 4; ++g) {
+      const float4 t = __ldg(q + i * (KT / 4) + g);
+      qs[4 * g] = t.x; qs[4 * g + 1] = t.y; qs[4 * g + 2] = t.z; qs[4 * g + 3] = t.w;
+    }
+    const int fi = (i >> sh) & mk;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const float4 y = *reinterpret_cast<const float4*>(base[u] + i * w + ((cq[u] ^ fi) << 2));
+      const float2 y0 = make_float2(y.x, y.y), y1 = make_float2(y.z, y.w);
+#pragma unroll
+      for (int o = 0; o < OG; ++o) {
+        acc[u][o][0] = __ffma2_rn(make_float2(qs[o], qs[o]), y0, acc[u][o][0]);
+        acc[u][o][1] = __ffma2_rn(make_float2(qs[o], qs[o]), y1, acc[u][o][1]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < CPT; ++u) {
+    if (!ok[u]) continue;
+#pragma unroll
+    for (int o = 0; o < OG; ++o) {
+      const int r = og * OG + o;  // output row
+      *reinterpret_cast<float4*>(base[u] + r * w + ((cq[u] ^ ((r >> sh) & mk)) << 2)) =
+          make_float4(acc[u][o][0].x, acc[u][o][0].y, acc[u][o][1].x, acc[u][o][1].y);
+    }
+  }
+  __syncthreads();
+}
+
 // Output of the column pass: packed blocks (OUT 0, at sOff[b] * 16), or blocks inside a
 // frame (at sAux[b] * 4, row stride `stride`) as FP32 (OUT 1) or rounded int16 (OUT 2).
 template <int H, int W, bool INV, int THREADS, int OUT>
@@ -649,6 +777,13 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
     {
       TfDev tf = sTf[k & 1][0];
       if constexpr (MULTI) tf.kind = KIND_NONE;  // the rows get the plain DCT-2 first
+      if constexpr (INV) {
+        if (tf.kind >= KIND_POST && post_inv_tiled(tf.kt, w)) {
+          if (w == 16) post_inv_rows_tile<16, 8, THREADS>(tf, a.params, buf, nb * h, h);
+          else if (w == 32) post_inv_rows_tile<32, 16, THREADS>(tf, a.params, buf, nb * h, h);
+          else post_inv_rows_tile<64, 32, THREADS>(tf, a.params, buf, nb * h, h);
+        }
+      }
       if constexpr (F32_IN) {
         switch (w) {
           case 4: row_pass<4, INV, THREADS, false>(tf, a.params, buf, nb, h); break;
@@ -701,6 +836,13 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
       const TfDev tf = sTf[k & 1][1];
       const uint32_t* aux = sAux[AUX ? (k & 1) : 0] + (td.blk_begin & 3);
       const int st = (int)a.frame_stride;
+      if constexpr (INV) {
+        if (tf.kind >= KIND_POST && post_inv_tiled(tf.kt, h)) {
+          if (h == 16) post_inv_cols_tile<16, 8, THREADS>(tf, a.params, buf, nb, w);
+          else if (h == 32) post_inv_cols_tile<32, 16, THREADS>(tf, a.params, buf, nb, w);
+          else post_inv_cols_tile<64, 32, THREADS>(tf, a.params, buf, nb, w);
+        }
+      }
       switch (h) {
         case 4: col_dispatch<4, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
         case 8: col_dispatch<8, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;

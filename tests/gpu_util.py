@@ -66,6 +66,18 @@ def check_forward(y, wl, blocks=None):
     return float(np.max(errs / np.maximum(norms, 1e-300)))
 
 
+def check_inverse(y, xr, wl, blocks=None):
+    """The GPU inverse of the GPU forward's FP32 coefficients y against the oracle's FP64
+    inverse of the same y: |X_gpu - X_oracle|_2 <= REL_TOL * |y|_2 per block."""
+    blocks = wl.blocks if blocks is None else blocks
+    ref = oracle.inverse_blocks(y, blocks, wl.tfs)
+    errs, norms = per_block_errors(xr, ref, y, blocks)
+    bad = errs > REL_TOL * norms
+    assert not bad.any(), (f"{bad.sum()} blocks over tolerance (inverse); worst ratio "
+                           f"{np.max(errs / np.maximum(norms, 1e-300)):.3e}")
+    return float(np.max(errs / np.maximum(norms, 1e-300)))
+
+
 def check_roundtrip(xr, wl, blocks=None, tol=RT_TOL):
     blocks = wl.blocks if blocks is None else blocks
     err = 0.0

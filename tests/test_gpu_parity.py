@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import REL_TOL, RT_TOL, check_forward, check_roundtrip, run_gpu, sub_workload
+from gpu_util import REL_TOL, RT_TOL, check_forward, check_inverse, check_roundtrip, run_gpu, sub_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +50,7 @@ def make_workload(tfs, sizes, seed=0, clip=1023, order=None, gap=0):
 def full_check(wl):
     y, xr = run_gpu(wl)
     worst = check_forward(y, wl)
+    check_inverse(y, xr, wl)
     rt = check_roundtrip(xr, wl)
     return worst, rt
 
@@ -96,6 +97,26 @@ def test_post_block_sizes(N, K):
     tfs = [synth.random_post(rng, N, int(rng.integers(4)), K), synth.random_post(rng, N, 0, K)]
     sizes = [(N, N, 0, 1)] * 5 + [(N, N, 1, 0)] * 3
     full_check(make_workload(tfs, sizes, seed=K))
+
+
+def test_tile_wide_inverse_post_blocks():
+    """Inverse post blocks of padded size n / 2 on 16-, 32- and 64-sample lines run over the
+    whole tile before the line pass (rows and columns); K below n / 2 pads to the same size.
+    Every block shape that uses them, in full and partial tiles, against the oracle's inverse."""
+    rng = np.random.default_rng(77)
+    tfs = [synth.Tf(n=4, core=1), synth.random_post(rng, 8, 2, 3),
+           synth.random_post(rng, 16, 0, 8), synth.random_post(rng, 16, 3, 5),
+           synth.random_post(rng, 32, 1, 16), synth.random_post(rng, 32, 2, 11),
+           synth.random_post(rng, 64, 0, 32), synth.random_post(rng, 64, 3, 20)]
+    by_n = {4: [0], 8: [1], 16: [2, 3], 32: [4, 5], 64: [6, 7]}
+    sizes = []
+    for w in synth.SIZES:
+        for h in synth.SIZES:
+            for rep in range(int(rng.integers(1, 4)) * (3 if w * h <= 256 else 1)):
+                sizes.append((w, h, int(rng.choice(by_n[w])), int(rng.choice(by_n[h]))))
+    order = rng.permutation(len(sizes))
+    worst, rt = full_check(make_workload(tfs, sizes, seed=77, order=order))
+    assert worst < REL_TOL and rt < RT_TOL
 
 
 @pytest.mark.parametrize("parities", [[], [1], [0], [1, 0, 1], [0, 1] * 32, [1] * 7])
