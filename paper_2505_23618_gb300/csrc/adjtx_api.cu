@@ -240,6 +240,19 @@ void materialise(const std::vector<TfHost>& tfs, std::vector<float>* params, std
     }
     devs->push_back(d);
   }
+  // transposes of the padded Q blocks (tile-wide forward post block), after all other tables so
+  // that those stay packed together
+  for (size_t n = 0; n < tfs.size(); ++n) {
+    const TfHost& t = tfs[n];
+    if (t.kind != ADJ_ADJ_POST_BLOCK && t.kind != ADJ_ADJ_DENSE) continue;
+    while (params->size() % 4) params->push_back(0.f);
+    (*devs)[n].qt_off = (uint32_t)params->size();
+    for (int j = 0; j < t.kt; ++j)
+      for (int i = 0; i < t.kt; ++i) {
+        double v = (i < t.k && j < t.k) ? t.q[i * t.k + j] : (i == j ? 1.0 : 0.0);
+        params->push_back((float)v);
+      }
+  }
   while (params->size() % 4) params->push_back(0.f);
   if (params->empty()) params->resize(4, 0.f);
 }

@@ -273,21 +273,25 @@ __device__ __forceinline__ void post_inv_k(T (&v)[N], const TfDev& tf, const flo
   }
 }
 
-// The inverse post blocks of the fused kernels with KT = n / 2 on 16- to 64-sample lines run
-// over the whole tile before the line pass (post_inv_rows_tile / post_inv_cols_tile in
-// adjtx_fused.cuh); their per-line form is then not compiled into those kernels.
+// Post blocks that run over the whole tile (post_rows_tile / post_cols_tile in adjtx_fused.cuh)
+// instead of per line; their per-line form is then not compiled into the fused kernels.  The
+// inverse's with KT = n / 2 on 16- to 64-sample lines, before the line pass:
 __host__ __device__ constexpr bool post_inv_tiled(int kt, int n) {
   return (n == 16 && kt == 8) || (n == 32 && kt == 16) || (n == 64 && kt == 32);
 }
 
-template <int N, class T, class Dst>
+// The forward's only for 64-sample rows with KT = 32, after the row pass (over Qp^T, TfDev::qt_off;
+// for shorter lines and for columns the per-line form measured faster in the forward kernels).
+__host__ __device__ constexpr bool post_fwd_tiled(int kt, int n) { return n == 64 && kt == 32; }
+
+template <int N, bool TILED = false, class T, class Dst>
 __device__ __forceinline__ void post_fwd(const T (&v)[N], const TfDev& tf, const float* __restrict__ P,
                                          const Dst& dst) {
   switch (tf.kt) {
     case 4: post_fwd_k<N, 4>(v, tf, P, dst); break;
     case 8: if constexpr (N >= 8) { post_fwd_k<N, 8>(v, tf, P, dst); } break;
     case 16: if constexpr (N >= 16) { post_fwd_k<N, 16>(v, tf, P, dst); } break;
-    case 32: if constexpr (N >= 32) { post_fwd_k<N, 32>(v, tf, P, dst); } break;
+    case 32: if constexpr (N >= 32 && !(TILED && post_fwd_tiled(32, N))) { post_fwd_k<N, 32>(v, tf, P, dst); } break;
     default: if constexpr (N >= 64) { post_fwd_k<N, 64>(v, tf, P, dst); } break;
   }
 }
@@ -482,7 +486,9 @@ struct DstGCol {
 // ---------------------------------------------------------------------------------
 // One line of a pass.  Forward: A (band), B (core), C (post).  Inverse: C^T, B^T, A^T.
 // ---------------------------------------------------------------------------------
-template <int N, bool INV, bool I16, class T = float, class Src, class Dst>
+// TILED (forward passes of the fused kernels): a post block that post_fwd_tiled selects is left
+// out here and applied over the whole tile afterwards (the line's core outputs are stored).
+template <int N, bool INV, bool I16, class T = float, bool TILED = false, class Src, class Dst>
 __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __restrict__ P,
                                                const Src& src, const Dst& dst) {
   T v[N];
@@ -494,8 +500,8 @@ __device__ __forceinline__ void line_transform(const TfDev& tf, const float* __r
   if constexpr (!INV) {
     if (tf.kind == KIND_BAND) band<N, false>(v, tf, P);
     if (tf.kind != KIND_DENSE) core_apply<N>(tf.core, v);
-    if (tf.kind >= KIND_POST) {
-      post_fwd<N>(v, tf, P, dst);
+    if (tf.kind >= KIND_POST && !(TILED && post_fwd_tiled(tf.kt, N))) {
+      post_fwd<N, TILED>(v, tf, P, dst);
     } else {
       dst.template store<N>(v);
     }

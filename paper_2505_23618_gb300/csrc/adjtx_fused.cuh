@@ -259,13 +259,13 @@ __device__ __forceinline__ void row_pass(const TfDev& tf, const float* __restric
       const int l2 = l + half;
       Pair<RowSw> row{RowSw{buf + l * W, ((l & (h - 1)) >> SH) & MK},
                       RowSw{buf + l2 * W, ((l2 & (h - 1)) >> SH) & MK}};
-      line_transform<W, INV, I16, float2>(tf, P, row, row);
+      line_transform<W, INV, I16, float2, !INV>(tf, P, row, row);
     }
   } else {
     for (int l = threadIdx.x; l < nlines; l += THREADS) {
       const int r = l & (h - 1);
       RowSw row{buf + l * W, (r >> SH) & MK};
-      line_transform<W, INV, I16>(tf, P, row, row);
+      line_transform<W, INV, I16, float, !INV>(tf, P, row, row);
     }
   }
 }
@@ -284,27 +284,27 @@ __device__ __forceinline__ void row_pass_s16(const TfDev& tf, const float* __res
       const Pair<RowS16<W>> src{RowS16<W>{S + l * W, s16_swz<W>(l)}, RowS16<W>{S + l2 * W, s16_swz<W>(l2)}};
       const Pair<RowSw> dst{RowSw{buf + l * W, ((l & (h - 1)) >> SH) & MK},
                             RowSw{buf + l2 * W, ((l2 & (h - 1)) >> SH) & MK}};
-      line_transform<W, false, true, float2>(tf, P, src, dst);
+      line_transform<W, false, true, float2, true>(tf, P, src, dst);
     }
   } else {
     for (int l = threadIdx.x; l < nlines; l += THREADS) {
       const RowS16<W> src{S + l * W, s16_swz<W>(l)};
       const RowSw dst{buf + l * W, ((l & (h - 1)) >> SH) & MK};
-      line_transform<W, false, true>(tf, P, src, dst);
+      line_transform<W, false, true, float, true>(tf, P, src, dst);
     }
   }
 }
 
 // ---------------------------------------------------------------------------------
-// Inverse post block C^T over a whole tile (Section 2.2): u_j = sum_i Qp[i][j] y_i on the first
-// KT values of every line, i.e. U = Y Qp for the tile's lines at once.  Each thread computes
-// an LG-line x OG-output block with OG/2 FP32x2 accumulators per line, reading its lines' y_i
-// from the tile and row i of Qp (OG consecutive entries, 16-byte loads) once per i, so every Q
-// entry loaded serves LG lines; then all threads write their outputs back in place.
+// Post block over a whole tile (Section 2.2): out_j = sum_i M[i][j] in_i on the first KT values
+// of every line, i.e. OUT = IN M for the tile's lines at once, with M = Qp for the inverse (C^T,
+// before the line pass) and M = Qp^T for the forward (C, after it).  Each thread computes an
+// LG-line x OG-output block with OG/2 FP32x2 accumulators per line, reading its lines' in_i from
+// the tile and row i of M (OG consecutive entries, 16-byte loads) once per i, so every entry
+// loaded serves LG lines; then all threads write their outputs back in place.
 // ---------------------------------------------------------------------------------
 template <int W, int KT, int THREADS>
-__device__ __forceinline__ void post_inv_rows_tile(const TfDev& tf, const float* __restrict__ P, float* buf,
-                                                   int nlines, int h) {
+__device__ __forceinline__ void post_rows_tile(const float* __restrict__ qtab, float* buf, int nlines, int h) {
   constexpr int SH = sw_shift(W), MK = sw_mask(W);
   constexpr int OG = 8;                                         // outputs per thread
   constexpr int NOG = KT / OG;                                  // output groups
@@ -327,7 +327,7 @@ __device__ __forceinline__ void post_inv_rows_tile(const TfDev& tf, const float*
   for (int j = 0; j < LG; ++j)
 #pragma unroll
     for (int e = 0; e < OG / 2; ++e) acc[j][e] = make_float2(0.f, 0.f);
-  const float4* q = reinterpret_cast<const float4*>(P + tf.q_off) + og * (OG / 4);
+  const float4* q = reinterpret_cast<const float4*>(qtab) + og * (OG / 4);
 #pragma unroll 4
   for (int i = 0; i < KT; ++i) {
     float4 qi[OG / 4];
@@ -358,12 +358,11 @@ __device__ __forceinline__ void post_inv_rows_tile(const TfDev& tf, const float*
   __syncthreads();
 }
 
-// The same along the columns: u_j = sum_i Qp[i][j] y_i down each column (rows i < KT of every
-// block), U = Qp^T Y per block.  A thread holds 4 adjacent columns (one 16-byte chunk of a row,
+// The same along the columns: out_j = sum_i M[i][j] in_i down each column (rows i < KT of every
+// block).  A thread holds 4 adjacent columns (one 16-byte chunk of a row,
 // two FP32x2 lanes) x OG outputs for CPT chunks.
 template <int H, int KT, int THREADS>
-__device__ __forceinline__ void post_inv_cols_tile(const TfDev& tf, const float* __restrict__ P, float* buf,
-                                                   int nb, int w) {
+__device__ __forceinline__ void post_cols_tile(const float* __restrict__ qtab, float* buf, int nb, int w) {
   constexpr int OG = 8;
   constexpr int NOG = KT / OG;
   constexpr int G = THREADS / NOG;                              // chunk-column groups
@@ -388,7 +387,7 @@ __device__ __forceinline__ void post_inv_cols_tile(const TfDev& tf, const float*
   for (int u = 0; u < CPT; ++u)
 #pragma unroll
     for (int o = 0; o < OG; ++o) acc[u][o][0] = acc[u][o][1] = make_float2(0.f, 0.f);
-  const float4* q = reinterpret_cast<const float4*>(P + tf.q_off) + og * (OG / 4);
+  const float4* q = reinterpret_cast<const float4*>(qtab) + og * (OG / 4);
 #pragma unroll 4
   for (int i = 0; i < KT; ++i) {
     float qs[OG];
@@ -426,7 +425,7 @@ __device__ __forceinline__ void post_inv_cols_tile(const TfDev& tf, const float*
 // Output of the column pass: packed blocks (OUT 0, at sOff[b] * 16), or blocks inside a
 // frame (at sAux[b] * 4, row stride `stride`) as FP32 (OUT 1) or rounded int16 (OUT 2).
 template <int H, int W, bool INV, int THREADS, int OUT>
-__device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restrict__ P, const float* buf,
+__device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restrict__ P, float* buf,
                                          const uint32_t* sOff, const uint32_t* sAux, float* __restrict__ out, int nb,
                                          int stride) {
   constexpr int lgw = ilog2(W);
@@ -463,7 +462,7 @@ __device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restric
 }
 
 template <int H, bool INV, int THREADS, int OUT>
-__device__ __forceinline__ void col_dispatch(const TfDev& tf, const float* __restrict__ P, const float* buf,
+__device__ __forceinline__ void col_dispatch(const TfDev& tf, const float* __restrict__ P, float* buf,
                                              const uint32_t* sOff, const uint32_t* sAux, float* __restrict__ out,
                                              int nb, int w, int stride) {
   switch (w) {
@@ -779,9 +778,9 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
       if constexpr (MULTI) tf.kind = KIND_NONE;  // the rows get the plain DCT-2 first
       if constexpr (INV) {
         if (tf.kind >= KIND_POST && post_inv_tiled(tf.kt, w)) {
-          if (w == 16) post_inv_rows_tile<16, 8, THREADS>(tf, a.params, buf, nb * h, h);
-          else if (w == 32) post_inv_rows_tile<32, 16, THREADS>(tf, a.params, buf, nb * h, h);
-          else post_inv_rows_tile<64, 32, THREADS>(tf, a.params, buf, nb * h, h);
+          if (w == 16) post_rows_tile<16, 8, THREADS>(a.params + tf.q_off, buf, nb * h, h);
+          else if (w == 32) post_rows_tile<32, 16, THREADS>(a.params + tf.q_off, buf, nb * h, h);
+          else post_rows_tile<64, 32, THREADS>(a.params + tf.q_off, buf, nb * h, h);
         }
       }
       if constexpr (F32_IN) {
@@ -800,6 +799,13 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
           case 32: row_pass_s16<32, THREADS>(tf, a.params, S, buf, nb, h); break;
           default: row_pass_s16<64, THREADS>(tf, a.params, S, buf, nb, h); break;
         }
+      }
+    }
+    if constexpr (!INV && !MULTI) {
+      const TfDev& th = sTf[k & 1][0];
+      if (th.kind >= KIND_POST && post_fwd_tiled(th.kt, w)) {
+        __syncthreads();
+        post_rows_tile<64, 32, THREADS>(a.params + th.qt_off, buf, nb * h, h);
       }
     }
     // (4)
@@ -838,9 +844,9 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
       const int st = (int)a.frame_stride;
       if constexpr (INV) {
         if (tf.kind >= KIND_POST && post_inv_tiled(tf.kt, h)) {
-          if (h == 16) post_inv_cols_tile<16, 8, THREADS>(tf, a.params, buf, nb, w);
-          else if (h == 32) post_inv_cols_tile<32, 16, THREADS>(tf, a.params, buf, nb, w);
-          else post_inv_cols_tile<64, 32, THREADS>(tf, a.params, buf, nb, w);
+          if (h == 16) post_cols_tile<16, 8, THREADS>(a.params + tf.q_off, buf, nb, w);
+          else if (h == 32) post_cols_tile<32, 16, THREADS>(a.params + tf.q_off, buf, nb, w);
+          else post_cols_tile<64, 32, THREADS>(a.params + tf.q_off, buf, nb, w);
         }
       }
       switch (h) {

@@ -30,7 +30,8 @@ struct TfDev {
   uint32_t csl_off;   // float4 index of the per-layer table: layer l's (cos, sin) pairs at
                       // float4 csl_off + l * n / 4, two rotations a float4, an odd layer
                       // padded with one unused pair
-  uint32_t pad[4];
+  uint32_t qt_off;    // float index of the transpose of the padded Q (tile-wide forward post)
+  uint32_t pad[3];
 };
 static_assert(sizeof(TfDev) == 64, "TfDev layout");
 

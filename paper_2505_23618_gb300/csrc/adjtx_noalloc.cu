@@ -45,7 +45,8 @@ constexpr size_t kTfOff = kRangeOff + 256;                           // 2 TfDev 
 constexpr size_t kParamOff = kTfOff + 256;                            // FP32 parameters
 // A transform carries a band or a post block, never both.  A band has at most 64 layers x 32
 // (cos, sin) pairs, stored twice (back to back, and per layer padded to n / 2 pairs): 8192
-// floats; a post block at most 64 x 64 = 4096.  Plus alignment padding.
+// floats; a post block at most 64 x 64 = 4096, stored with its transpose: 8192.  Plus alignment
+// padding.
 constexpr size_t kMaxParamFloats = 2 * 8200 + 32;
 constexpr size_t kTileOff = kParamOff + ((kMaxParamFloats * 4 + 255) / 256) * 256;
 constexpr size_t kTileBytes = (size_t)ADJ_NOALLOC_MAX_BLOCKS * sizeof(TileDev);
@@ -171,6 +172,10 @@ int pack_tf(const adj_1d_desc_t* d, const char* name, TfDev* rec, float* params,
     rec->q_off = (uint32_t)np;
     for (int i = 0; i < kt; ++i)
       for (int j = 0; j < kt; ++j)
+        params[np++] = (float)((i < k && j < k) ? d->q[i * k + j] : (i == j ? 1.0 : 0.0));
+    rec->qt_off = (uint32_t)np;
+    for (int j = 0; j < kt; ++j)
+      for (int i = 0; i < kt; ++i)
         params[np++] = (float)((i < k && j < k) ? d->q[i * k + j] : (i == j ? 1.0 : 0.0));
   }
   *n_params = np;

@@ -89,6 +89,10 @@ def test_noalloc_matches_plan_forward_and_oracle_in_a_row():
         # 4x4 again, a count that leaves the last tile partly filled
         (synth.Tf(n=4, core=synth.CORE_DCT2),
          synth.random_band(rng, 4, synth.CORE_DST3, [1, 0, 1, 0]), MAX_BLOCKS - 77),
+        # 64x16 with a 64-point K = 32 post block along the rows (applied over the whole tile,
+        # from the transposed Q the call uploads), 4 blocks per tile, 517 not a multiple of it
+        (synth.random_post(rng, 64, synth.CORE_DST2, 32),
+         synth.random_post(rng, 16, synth.CORE_DCT2, 8), 517),
     ]
     for tf_h, tf_v, n in calls:
         _check_call(lib, rng, tf_h, tf_v, n)
