@@ -280,8 +280,9 @@ __host__ __device__ constexpr bool post_inv_tiled(int kt, int n) {
   return (n == 16 && kt == 8) || (n == 32 && kt == 16) || (n == 64 && kt == 32);
 }
 
-// The forward's only for 64-sample rows with KT = 32, after the row pass (over Qp^T, TfDev::qt_off;
-// for shorter lines and for columns the per-line form measured faster in the forward kernels).
+// The forward's only for 64-sample lines with KT = 32 (rows after the row pass, columns after the
+// column pass has written its outputs back into the tile; over Qp^T, TfDev::qt_off): for shorter
+// lines the per-line form measured faster in the 128-register forward kernels.
 __host__ __device__ constexpr bool post_fwd_tiled(int kt, int n) { return n == 64 && kt == 32; }
 
 template <int N, bool TILED = false, class T, class Dst>
@@ -375,6 +376,16 @@ struct ColSw {
   }
   __device__ __forceinline__ float get_rt(int i) const {
     return blk[i * W + ((((c >> 2) ^ ((i >> SH) & MK))) << 2) + (c & 3)];
+  }
+  // the column written back in place (forward columns whose post block runs over the tile)
+  template <int N>
+  __device__ __forceinline__ void store(const float (&v)[N]) const {
+#pragma unroll
+    for (int i = 0; i < N; ++i) const_cast<float*>(p[(i >> SH) & MK])[i * W] = v[i];
+  }
+  __device__ __forceinline__ void put(int i, float x) const { const_cast<float*>(p[(i >> SH) & MK])[i * W] = x; }
+  __device__ __forceinline__ void put_rt(int i, float x) const {
+    const_cast<float*>(blk)[i * W + ((((c >> 2) ^ ((i >> SH) & MK))) << 2) + (c & 3)] = x;
   }
 };
 

@@ -422,6 +422,20 @@ __device__ __forceinline__ void post_cols_tile(const float* __restrict__ qtab, f
   __syncthreads();
 }
 
+// Copy a transformed tile (swizzled rows) to its packed blocks: 16-byte loads and streaming
+// stores, a warp covering consecutive chunks of a block.
+template <int THREADS>
+__device__ __forceinline__ void copy_tile_out(const float* buf, const uint32_t* sOff, float* __restrict__ out,
+                                              int nb, int w, int h) {
+  const int sh = sw_shift(w), mk = sw_mask(w), lgq = lg2(w >> 2), lgb = lgq + lg2(h);
+  const int total = nb << lgb;
+  for (int g = threadIdx.x; g < total; g += THREADS) {
+    const int b = g >> lgb, rq = g & ((1 << lgb) - 1), r = rq >> lgq, q = rq & ((w >> 2) - 1);
+    const float4 v = *reinterpret_cast<const float4*>(buf + b * (w * h) + r * w + ((q ^ ((r >> sh) & mk)) << 2));
+    __stcs(reinterpret_cast<float4*>(out + (size_t)sOff[b] * 16 + r * w + q * 4), v);
+  }
+}
+
 // Output of the column pass: packed blocks (OUT 0, at sOff[b] * 16), or blocks inside a
 // frame (at sAux[b] * 4, row stride `stride`) as FP32 (OUT 1) or rounded int16 (OUT 2).
 template <int H, int W, bool INV, int THREADS, int OUT>
@@ -430,6 +444,8 @@ __device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restric
                                          int stride) {
   constexpr int lgw = ilog2(W);
   const int nlines = nb * W;
+  // forward 64-sample columns with K = 32: core outputs back into the tile, post block over it
+  const bool tiled = !INV && H == 64 && tf.kind >= KIND_POST && post_fwd_tiled(tf.kt, H);
   if constexpr (H <= 32) {
     // adjacent columns (c, c + 1) as one packed pair: 8-byte shared loads and global stores
     const int pairs = nlines >> 1;
@@ -449,7 +465,9 @@ __device__ __forceinline__ void col_pass(const TfDev& tf, const float* __restric
     for (int l = threadIdx.x; l < nlines; l += THREADS) {
       const int b = l >> lgw, c = l & (W - 1);
       ColSw<W> src(buf + b * (W * H), c);
-      if constexpr (OUT == 0) {
+      if (!INV && OUT == 0 && tiled) {
+        line_transform<H, false, false, float, true>(tf, P, src, src);
+      } else if constexpr (OUT == 0) {
         line_transform<H, INV, false>(tf, P, src, DstGCol<W>{out + (size_t)sOff[b] * 16 + c});
       } else if constexpr (OUT == 1) {
         line_transform<H, INV, false>(tf, P, src, DstFrame{out + (size_t)sAux[b] * 4 + c, stride});
@@ -855,6 +873,13 @@ __global__ void __launch_bounds__(THREADS, fused_ctas_per_sm(INV, MODE) * 64 / T
         case 16: col_dispatch<16, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
         case 32: col_dispatch<32, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
         default: col_dispatch<64, INV, THREADS, OUT>(tf, a.params, buf, offs, aux, a.out, nb, w, st); break;
+      }
+      if constexpr (!INV && OUT == 0) {
+        if (h == 64 && tf.kind >= KIND_POST && post_fwd_tiled(tf.kt, h)) {
+          __syncthreads();
+          post_cols_tile<64, 32, THREADS>(a.params + tf.qt_off, buf, nb, w);
+          copy_tile_out<THREADS>(buf, offs, a.out, nb, w, h);
+        }
       }
     }
   }
