@@ -53,3 +53,18 @@ def test_line_and_block_flops():
     # block 0: 8 rows of 16 (band) + 16 columns of 8 (post); block 1: 8 rows of 4 + 4 columns of 8
     want = 8 * 300 + 16 * 78 + 8 * 16 + 4 * 128
     assert bench.alg_flops(blocks, tfs) == want
+
+
+def test_profiled_traffic_only_for_the_source_it_was_taken_on(monkeypatch):
+    """The bench reports the committed ncu traffic counters only while the kernel source hash
+    matches the one they were captured on; any change to the sources makes them null."""
+    with open(os.path.join(HERE, "..", "profiles", "traffic.txt")) as f:
+        lines = f.read().splitlines()
+    key = [ln.split()[-1] for ln in lines if ln.startswith("source_hash")][0]
+    vals = {ln.split()[0]: float(ln.split()[1]) for ln in lines
+            if ln and not ln.startswith("#") and not ln.startswith("source_hash")}
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: key)
+    for name, v in vals.items():
+        assert bench.profiled_traffic(name) == v
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert all(bench.profiled_traffic(name) is None for name in vals)
